@@ -1,0 +1,258 @@
+/*
+ * spmv_gb300.h -- C ABI of the GB300 (sm_103a) wide/tall sparse product library.
+ *
+ * Implements the two products of Eckstein & Matyasfalvi, "Efficient
+ * Distributed-Memory Parallel Matrix-Vector Multiplication with Wide or Tall
+ * Unstructured Sparse Matrices" (arXiv 1812.00904):
+ *
+ *   SpMV   y = A x          (Sec. I)        A is m x n with Z nonzeros
+ *   SpVTM  u^T = v^T A      (Sec. I)
+ *
+ * for a wide matrix stored column-major (CSC, m << n) or a tall matrix stored
+ * row-major (CSR, m >> n; Sec. II, "reversing the roles of rows and columns").
+ * The nonzeros are split into P contiguous, equally sized chunks whatever the
+ * column boundaries (Sec. II); chunks that share a column (an "overlap zone")
+ * combine their partial dot products through per-chunk carry records and a
+ * fixed-order reduction (Sec. IV-A), with the zones numbered by the set-up
+ * scans of Sec. IV-B.  On the GPU a chunk is the work of one warp.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Indices are 0-based int32.  ptr has (n+1) entries for CSC, (m+1) for CSR;
+ *    ptr[0] = 0, ptr non-decreasing, ptr[last] = nnz < 2^31.  idx entries lie in
+ *    [0, m) for CSC and [0, n) for CSR.  Repeated indices in one column (row)
+ *    add up; indices need not be sorted; empty columns (rows) are allowed.
+ *  - Element types (spmv_dtype): values and vectors are one of the pairs
+ *    (F64, F64), (F32, F32), (BF16, F32), (F16, F32).  Accumulation is FP32 for
+ *    the last three and FP64 for the first; cross-chunk combines are FP64.
+ *  - A plan BORROWS the caller's device arrays ptr/idx/vals: they must stay
+ *    allocated and unchanged (values may change between calls) until
+ *    spmv_plan_destroy.  The plan owns only its workspace.
+ *  - Device pointers must be 16-byte aligned (cudaMalloc and torch allocations
+ *    are); a misaligned pointer is rejected with SPMV_ERR_INVALID_ARG.
+ *  - Vector arguments of spmv, spvtm and spmv_dvalues may be device pointers or
+ *    host pointers (pinned or pageable).  With device pointers the call is
+ *    asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ *    With host pointers the library copies through its own device buffers and
+ *    the call returns after the result has landed in host memory.
+ *  - Outputs are overwritten (no alpha/beta).
+ *  - No call aborts the process.  Failures return a status; spmv_last_error()
+ *    gives a thread-local message.  Kernels never trap: a device-side failure
+ *    (an index out of range, a staging wait that timed out) sets an error word
+ *    that spmv_check() reports as SPMV_ERR_DEVICE.
+ */
+#ifndef SPMV_GB300_H
+#define SPMV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, bad size or dtype pair */
+    SPMV_ERR_BAD_MATRIX = 2,   /* ptr/idx fail the structural checks above */
+    SPMV_ERR_OOM = 3,          /* a device or host allocation failed */
+    SPMV_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    SPMV_ERR_DEVICE = 5,       /* a kernel reported a failure through the error word */
+    SPMV_ERR_TIMEOUT = 6,      /* serve_wait ran out of time */
+    SPMV_ERR_BUSY = 7,         /* serving: no room (HBM budget / queue) right now */
+    SPMV_ERR_UNSUPPORTED = 8,  /* valid request this build does not implement */
+    SPMV_ERR_NOT_FOUND = 9     /* unknown matrix or request id */
+} spmv_status;
+
+typedef enum { SPMV_CSC_WIDE = 0, SPMV_CSR_TALL = 1 } spmv_layout;            /* Sec. II */
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2, SPMV_F16 = 3 } spmv_dtype;
+typedef enum { SPMV_OP_AX = 0, SPMV_OP_VTA = 1 } spmv_op;                       /* Sec. I */
+
+typedef struct spmv_plan_s *spmv_plan_t;
+
+/* Plan flags. */
+#define SPMV_PLAN_NO_VALIDATE 0x1u  /* skip the structural checks of ptr/idx */
+#define SPMV_PLAN_PROFILE 0x2u      /* time every kernel launch with CUDA events (spmv_profile_read) */
+#define SPMV_PLAN_SHORT_IN_GLOBAL 0x4u /* keep the short vector in global memory even when it fits on chip */
+
+/* Optional tuning of a plan; zero fields take the defaults. */
+typedef struct {
+    int32_t chunks;        /* P, the number of nonzero chunks (Sec. II); 0 = one per warp of a full GPU wave */
+    int32_t warps_per_cta; /* warps (chunks) per CTA; 0 = chosen from the shared-memory budget */
+    int32_t tile_items;    /* merge items (nonzeros + column ends) per staged tile, 64..992, multiple of 32 */
+    int32_t stages;        /* staging buffers per warp, 2..8 */
+} spmv_plan_opts;
+
+/* Summary of a plan (spmv_plan_info). */
+typedef struct {
+    int64_t m, n, nnz;
+    int32_t layout, val_dtype, vec_dtype;
+    int32_t chunks;            /* P */
+    int32_t ctas, warps_per_cta, tile_items, stages;
+    int32_t tiles;             /* staged tiles over all chunks */
+    int32_t zones;             /* z, overlap zones (Sec. II), z <= P-1 */
+    int32_t max_zone_size;     /* V = max |S_k| (Sec. IV-A) */
+    int32_t short_on_chip;     /* 1 if the short vector lives in shared memory */
+    int32_t batch_width;       /* vectors per pass of spmv_batch (1..8) */
+    int64_t max_chunk_nnz, min_chunk_nnz;
+    double imbalance;          /* Delta = P (max - min) / Z (Sec. VI), 0 when Z = 0 */
+    int64_t workspace_bytes;   /* device bytes owned by the plan */
+    double setup_ms;           /* device time of the set-up kernels */
+} spmv_plan_info_t;
+
+/* Per-chunk set-up values (spmv_plan_chunks), one per chunk p_c (Sec. IV-B, Table III). */
+typedef struct {
+    int64_t nz_begin, nz_end;   /* nonzeros [begin, end) of the chunk (Sec. II rule) */
+    int32_t jf, jl;             /* first / last column (row for CSR) j^f, j^l; -1 if the chunk is empty */
+    int32_t needLeft, needRight, leftGroupEnd, rightGroup, leftGroup, procsOnLeft, procsOnRight;
+} spmv_chunk_t;
+
+/*
+ * spmv_plan -- build the execution plan of one matrix (Sec. II partition and
+ * Sec. IV-B overlap-zone set-up, computed on the device).
+ *   out        receives the plan handle (owned by the caller; free with spmv_plan_destroy)
+ *   m, n, nnz  matrix shape and nonzero count (0 <= nnz < 2^31; m, n < 2^31)
+ *   layout     SPMV_CSC_WIDE or SPMV_CSR_TALL
+ *   ptr, idx   device arrays (int32), see conventions; borrowed
+ *   vals       device array of nnz values of type val_dtype; borrowed
+ *   vec_dtype  element type of the dense vectors
+ *   stream     cudaStream_t for the set-up kernels; the call synchronizes it once
+ *   flags      SPMV_PLAN_* bits
+ * Errors: SPMV_ERR_INVALID_ARG, SPMV_ERR_BAD_MATRIX (checked unless
+ * SPMV_PLAN_NO_VALIDATE), SPMV_ERR_OOM, SPMV_ERR_CUDA, SPMV_ERR_UNSUPPORTED.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+spmv_status spmv_plan(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout,
+                      const int32_t *ptr, const int32_t *idx, const void *vals,
+                      int32_t val_dtype, int32_t vec_dtype, void *stream, uint32_t flags);
+
+/* spmv_plan with explicit tuning (opts may be NULL). */
+spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout,
+                         const int32_t *ptr, const int32_t *idx, const void *vals,
+                         int32_t val_dtype, int32_t vec_dtype, void *stream, uint32_t flags,
+                         const spmv_plan_opts *opts);
+
+/* Release the plan's workspace.  Accepts NULL.  The caller's arrays are untouched. */
+spmv_status spmv_plan_destroy(spmv_plan_t plan);
+
+/* Copy the plan summary into *info (host memory). */
+spmv_status spmv_plan_info(spmv_plan_t plan, spmv_plan_info_t *info);
+
+/* Copy the per-chunk set-up values of chunks [0, count) into out[] (host), count <= P. Synchronous. */
+spmv_status spmv_plan_chunks(spmv_plan_t plan, spmv_chunk_t *out, int32_t count);
+
+/*
+ * spmv -- y = A x (Sec. I; Sec. III for the chunked computation: every chunk
+ * accumulates A_(i) x_(i) into an on-chip copy of the short vector, and the
+ * per-CTA partial vectors are summed in FP64 in a fixed order).
+ *   x  n values of vec_dtype (device or host);  y  m values of vec_dtype (device or host), overwritten.
+ */
+spmv_status spmv(spmv_plan_t plan, const void *x, void *y, void *stream);
+
+/*
+ * spvtm -- u^T = v^T A (Sec. I; Sec. IV-A: every chunk dots its partial
+ * columns with v; columns split between chunks are completed from carry
+ * records, u_j = sum over S_k of v^T A_j^p, in FP64 and a fixed order).
+ *   v  m values of vec_dtype (device or host);  u  n values of vec_dtype (device or host), overwritten.
+ */
+spmv_status spvtm(spmv_plan_t plan, const void *v, void *u, void *stream);
+
+/*
+ * spmv_batch -- k products with one pass over the matrix per group of
+ * batch_width vectors (spmv_plan_info).  op = SPMV_OP_AX: Y = A X, vector b of
+ * X at in + b*ld_in (length n), of Y at out + b*ld_out (length m);
+ * op = SPMV_OP_VTA: U^T = V^T A with lengths m in, n out.  ld in elements,
+ * ld >= vector length and ld * element size a multiple of 16.  Device pointers
+ * only.  1 <= k <= 4096.  Every vector's result equals its single-vector
+ * product within the stated tolerances.
+ */
+spmv_status spmv_batch(spmv_plan_t plan, int32_t op, int32_t k, const void *in, int64_t ld_in,
+                       void *out, int64_t ld_out, void *stream);
+
+/*
+ * spmv_dvalues -- gradient of r^T A x with respect to the stored values:
+ * g[p] = r_i x_j for the nonzero at position p holding A_ij.  r has m entries,
+ * x has n (vec_dtype); g has nnz entries of the plan's val_dtype.  This is the
+ * d(values) part of the backward pass of y = A x (with r = dL/dy); the dx part
+ * is spvtm(plan, r).  Device or host pointers.
+ */
+spmv_status spmv_dvalues(spmv_plan_t plan, const void *r, const void *x, void *g, void *stream);
+
+/* Synchronize `stream`, then read and clear the plan's device error word.
+ * Returns SPMV_ERR_DEVICE (with a message) if any kernel flagged a failure. */
+spmv_status spmv_check(spmv_plan_t plan, void *stream);
+
+/* Kernel timers of a plan created with SPMV_PLAN_PROFILE.  kernel: 0 = chunk
+ * scatter (SpMV local), 1 = partial combine, 2 = chunk dot (SpVTM local),
+ * 3 = zone fixup, 4 = dvalues.  Synchronizes the device.  *ms = summed event
+ * time, *launches = number of timed launches. */
+spmv_status spmv_profile_read(spmv_plan_t plan, int32_t kernel, double *ms, int64_t *launches);
+spmv_status spmv_profile_reset(spmv_plan_t plan);
+
+/* Thread-local message for the last failing call of this thread ("" if none). */
+const char *spmv_last_error(void);
+
+/* Library version string. */
+const char *spmv_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of single products over resident matrices. */
+
+typedef struct serve_s *serve_t;
+
+/*
+ * serve_create -- start a serving runtime with its own scheduler thread.
+ *   hbm_budget_bytes  device bytes the resident matrices (and their plans) may use
+ *   k_max             most vectors coalesced into one multi-vector launch (1..64)
+ *   n_streams         CUDA streams that run launches concurrently (1..16)
+ */
+spmv_status serve_create(serve_t *out, uint64_t hbm_budget_bytes, int32_t k_max, int32_t n_streams);
+
+/* Register an existing plan (its arrays already on the device; never evicted).
+ * Its footprint counts against the budget: SPMV_ERR_BUSY if it does not fit. */
+spmv_status serve_register(serve_t srv, spmv_plan_t plan, int32_t *mat_id);
+
+/* Register a matrix held in HOST memory (borrowed until serve_destroy).  It is
+ * copied to the device and planned when a request needs it and the budget
+ * allows; idle host-registered matrices are evicted (least recently used) to
+ * admit others. */
+spmv_status serve_register_host(serve_t srv, int64_t m, int64_t n, int64_t nnz, int32_t layout,
+                                const int32_t *ptr, const int32_t *idx, const void *vals,
+                                int32_t val_dtype, int32_t vec_dtype, int32_t *mat_id);
+
+/*
+ * serve_submit -- queue k products of matrix mat_id: op = SPMV_OP_AX computes
+ * out_b = A in_b, SPMV_OP_VTA computes out_b^T = in_b^T A, vector b at
+ * in + b*len_in and out + b*len_out (device memory, vec_dtype, contiguous).
+ * Returns at once with *req_id.  The request joins the next launch of the same
+ * (matrix, op) with room; the buffers must stay valid until it completes.
+ */
+spmv_status serve_submit(serve_t srv, int32_t mat_id, int32_t op, int32_t k,
+                         const void *in, void *out, uint64_t *req_id);
+
+/* Non-blocking status: *done = 1 once the results are in `out`; *latency_ms =
+ * submit-to-completion time (valid when done).  A finished request that failed
+ * returns its error status. */
+spmv_status serve_poll(serve_t srv, uint64_t req_id, int32_t *done, double *latency_ms);
+
+/* Block until the request completes or timeout_ms passes (SPMV_ERR_TIMEOUT). */
+spmv_status serve_wait(serve_t srv, uint64_t req_id, int32_t timeout_ms);
+
+/* Counters of a serving runtime. */
+typedef struct {
+    int64_t submitted, completed, failed, vectors, launches;
+    int64_t admissions, evictions, resident_matrices;
+    uint64_t resident_bytes;
+    int32_t max_inflight_launches;
+} serve_stats_t;
+
+spmv_status serve_stats(serve_t srv, serve_stats_t *out);
+
+/* Stop the scheduler after the queued requests finish and free everything. */
+spmv_status serve_destroy(serve_t srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_GB300_H */

@@ -1,0 +1,655 @@
+// C ABI of libspmv_gb300 (declared in include/spmv_gb300.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "plan_impl.h"
+
+using namespace gbk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+int dtype_size(int t) {
+    switch (t) {
+        case SPMV_F64: return 8;
+        case SPMV_F32: return 4;
+        case SPMV_BF16: return 2;
+        case SPMV_F16: return 2;
+        default: return 0;
+    }
+}
+
+bool pair_supported(int vt, int xt) {
+    return (vt == SPMV_F64 && xt == SPMV_F64) || (vt == SPMV_F32 && xt == SPMV_F32) ||
+           (vt == SPMV_BF16 && xt == SPMV_F32) || (vt == SPMV_F16 && xt == SPMV_F32);
+}
+
+#define CUDA_TRY(expr)                                                                              \
+    do {                                                                                            \
+        cudaError_t _e = (expr);                                                                    \
+        if (_e != cudaSuccess)                                                                      \
+            return set_error(_e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM : SPMV_ERR_CUDA,        \
+                             std::string(#expr) + ": " + cudaGetErrorString(_e));                  \
+    } while (0)
+
+cudaError_t launch_stream(const spmv_plan_s *p, int mode, int kb, const LaunchArgs &a) {
+    switch (p->val_t) {
+        case SPMV_F64: return launch_stream_f64(mode, kb, a);
+        case SPMV_F32: return launch_stream_f32(mode, kb, a);
+        case SPMV_BF16: return launch_stream_bf16(mode, kb, a);
+        default: return launch_stream_f16(mode, kb, a);
+    }
+}
+
+int kb_template(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : 8; }
+
+// Kernel timers: bracket one launch with events when the plan profiles.
+struct ProfScope {
+    spmv_plan_s *p;
+    int kernel;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(spmv_plan_s *p_, int k, cudaStream_t s_) : p(p_), kernel(k), s(s_) {
+        if (p->flags & SPMV_PLAN_PROFILE) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            cudaEventRecord(b, s);
+            std::lock_guard<std::mutex> lk(p->prof_mu);
+            p->prof.push_back({kernel, a, b});
+        }
+    }
+};
+
+StreamParams base_params(const spmv_plan_s *p) {
+    StreamParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.idx = p->idx;
+    sp.vals = p->vals;
+    sp.pptr = p->pptr;
+    sp.nnz = (int)p->nnz;
+    sp.n_major = p->n_major;
+    sp.n_minor = p->n_minor;
+    sp.P = p->P;
+    sp.chunks = p->chunks;
+    sp.tiles = p->tiles;
+    sp.stage_bytes = p->stage_bytes;
+    sp.warp_bytes = p->warp_bytes;
+    sp.stages = p->S;
+    sp.pptr_len = p->pptr_len;
+    sp.table_bytes = p->table_bytes;
+    sp.rec_left = p->rec_left;
+    sp.rec_right = p->rec_right;
+    sp.err = p->err;
+    return sp;
+}
+
+enum PtrKind { PK_DEVICE, PK_HOST, PK_BAD };
+
+PtrKind classify(const void *ptr) {
+    if (!ptr) return PK_BAD;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PK_HOST;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return PK_DEVICE;
+    return PK_HOST;
+}
+
+}  // namespace
+
+namespace gbk {
+
+spmv_status set_error(spmv_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+size_t plan_footprint(const spmv_plan_s *p) {
+    return p->ws_bytes + (size_t)p->ntiles * sizeof(int2) + (size_t)p->nnz * (4 + p->sv) +
+           (size_t)(p->n_major + 1) * 4;
+}
+
+spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
+    const size_t out_bytes = (size_t)p->n_minor * p->sx;
+    if (p->nnz == 0 || p->n_major == 0) {
+        if (out_bytes)
+            for (int b = 0; b < kb; ++b) CUDA_TRY(cudaMemsetAsync(out[b], 0, out_bytes, s));
+        return SPMV_OK;
+    }
+    if (!p->onchip && kb > 1) {
+        for (int b = 0; b < kb; ++b) {
+            spmv_status st = run_scatter(p, 1, in + b, out + b, s);
+            if (st != SPMV_OK) return st;
+        }
+        return SPMV_OK;
+    }
+    LaunchArgs a;
+    a.sp = base_params(p);
+    a.sp.kb = kb;
+    for (int b = 0; b < kb; ++b) a.sp.vin[b] = in[b];
+    a.smemv = p->onchip;
+    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kb_template(kb) * p->sa, 128) : 0;
+    a.sp.part = p->part;
+    if (!p->onchip) CUDA_TRY(cudaMemsetAsync(p->part, 0, (size_t)p->n_minor * sizeof(double), s));
+    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
+    a.grid = p->ctas;
+    a.block = p->W * 32;
+    a.stream = s;
+    {
+        ProfScope ps(p, 0, s);
+        CUDA_TRY(launch_stream(p, MODE_SCATTER, kb, a));
+    }
+    {
+        ProfScope ps(p, 1, s);
+        const bool f64 = p->vec_t == SPMV_F64;
+        CUDA_TRY(launch_combine(f64, f64 || !p->onchip, p->part, p->onchip ? p->ctas : 1, p->n_minor, kb, out, s));
+    }
+    return SPMV_OK;
+}
+
+spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
+    const size_t out_bytes = (size_t)p->n_major * p->sx;
+    if (p->nnz == 0 || p->n_minor == 0) {
+        if (out_bytes)
+            for (int b = 0; b < kb; ++b) CUDA_TRY(cudaMemsetAsync(out[b], 0, out_bytes, s));
+        return SPMV_OK;
+    }
+    if (!p->onchip && kb > 1) {
+        for (int b = 0; b < kb; ++b) {
+            spmv_status st = run_segdot(p, 1, in + b, out + b, s);
+            if (st != SPMV_OK) return st;
+        }
+        return SPMV_OK;
+    }
+    LaunchArgs a;
+    a.sp = base_params(p);
+    a.sp.kb = kb;
+    for (int b = 0; b < kb; ++b) {
+        a.sp.vin[b] = in[b];
+        a.sp.vout[b] = out[b];
+    }
+    a.smemv = p->onchip;
+    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kb_template(kb) * p->sx, 128) : 0;
+    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
+    a.grid = p->ctas;
+    a.block = p->W * 32;
+    a.stream = s;
+    {
+        ProfScope ps(p, 2, s);
+        CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
+    }
+    if (p->z > 0) {
+        ProfScope ps(p, 3, s);
+        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, p->zones, p->z, p->rec_left, p->rec_right, p->P, kb, out, s));
+    }
+    return SPMV_OK;
+}
+
+static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, void *g, cudaStream_t s) {
+    if (p->nnz == 0) return SPMV_OK;
+    LaunchArgs a;
+    a.sp = base_params(p);
+    a.sp.kb = 1;
+    // CSC: g = r[row] * x[col] -> minor r, major x;  CSR: g = r[row] * x[col] -> minor x, major r
+    const bool csc = p->layout == SPMV_CSC_WIDE;
+    a.sp.vin[0] = csc ? r : x;
+    a.sp.vin[1] = csc ? x : r;
+    a.sp.vout[0] = g;
+    a.smemv = p->onchip;
+    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * p->sx, 128) : 0;
+    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
+    a.grid = p->ctas;
+    a.block = p->W * 32;
+    a.stream = s;
+    ProfScope ps(p, 4, s);
+    CUDA_TRY(launch_stream(p, MODE_DVALUES, 1, a));
+    return SPMV_OK;
+}
+
+spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *const *out, cudaStream_t s) {
+    const bool scatter = (op == SPMV_OP_AX) == (p->layout == SPMV_CSC_WIDE);
+    for (int g0 = 0; g0 < k; g0 += p->batch_width) {
+        const int kb = std::min(p->batch_width, k - g0);
+        spmv_status st = scatter ? run_scatter(p, kb, in + g0, out + g0, s) : run_segdot(p, kb, in + g0, out + g0, s);
+        if (st != SPMV_OK) return st;
+    }
+    return SPMV_OK;
+}
+
+}  // namespace gbk
+
+namespace {
+
+void free_plan(spmv_plan_s *p) {
+    if (!p) return;
+    for (auto &pr : p->prof) {
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
+    }
+    if (p->ws) cudaFree(p->ws);
+    if (p->tiles) cudaFree(p->tiles);
+    if (p->hin) cudaFree(p->hin);
+    if (p->hout) cudaFree(p->hout);
+    if (p->hg) cudaFree(p->hg);
+    delete p;
+}
+
+struct PlanGuard {
+    spmv_plan_s *p;
+    ~PlanGuard() { free_plan(p); }
+};
+
+// Runs `fn` on device pointers, staging host pointers through plan buffers.
+template <typename Fn>
+spmv_status with_staging(spmv_plan_s *p, const void *in, size_t in_bytes, void *out, size_t out_bytes,
+                         cudaStream_t s, Fn fn) {
+    // an empty vector may be NULL (torch gives zero-size tensors a null address)
+    const PtrKind ki = (in_bytes == 0 && !in) ? PK_DEVICE : classify(in);
+    const PtrKind ko = (out_bytes == 0 && !out) ? PK_DEVICE : classify(out);
+    if (ki == PK_BAD || ko == PK_BAD) return set_error(SPMV_ERR_INVALID_ARG, "null vector pointer");
+    if (ki == PK_DEVICE && ko == PK_DEVICE) {
+        if ((in && !aligned16(in)) || (out && !aligned16(out)))
+            return set_error(SPMV_ERR_INVALID_ARG, "device vector pointers must be 16-byte aligned");
+        return fn(in, out);
+    }
+    std::lock_guard<std::mutex> lk(p->host_mu);
+    const size_t cap = (size_t)std::max(p->m, p->n) * p->sx + 16;
+    if (!p->hin) CUDA_TRY(cudaMalloc(&p->hin, cap));
+    if (!p->hout) CUDA_TRY(cudaMalloc(&p->hout, cap));
+    const void *din = in;
+    void *dout = out;
+    if (ki == PK_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(p->hin, in, in_bytes, cudaMemcpyHostToDevice, s));
+        din = p->hin;
+    } else if (!aligned16(in)) {
+        return set_error(SPMV_ERR_INVALID_ARG, "device vector pointers must be 16-byte aligned");
+    }
+    if (ko == PK_HOST) dout = p->hout;
+    spmv_status st = fn(din, dout);
+    if (st != SPMV_OK) return st;
+    if (ko == PK_HOST) CUDA_TRY(cudaMemcpyAsync(out, dout, out_bytes, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *spmv_last_error(void) { return g_last_error.c_str(); }
+
+const char *spmv_version(void) { return "spmv_gb300 0.1 (sm_103a)"; }
+
+spmv_status spmv_plan(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout, const int32_t *ptr,
+                      const int32_t *idx, const void *vals, int32_t val_dtype, int32_t vec_dtype, void *stream,
+                      uint32_t flags) {
+    return spmv_plan_ex(out, m, n, nnz, layout, ptr, idx, vals, val_dtype, vec_dtype, stream, flags, nullptr);
+}
+
+spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout, const int32_t *ptr,
+                         const int32_t *idx, const void *vals, int32_t val_dtype, int32_t vec_dtype, void *stream,
+                         uint32_t flags, const spmv_plan_opts *opts) {
+    g_last_error.clear();
+    if (!out) return set_error(SPMV_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (layout != SPMV_CSC_WIDE && layout != SPMV_CSR_TALL) return set_error(SPMV_ERR_INVALID_ARG, "bad layout");
+    if (m < 0 || n < 0 || nnz < 0 || m >= (1ll << 31) - 64 || n >= (1ll << 31) - 64 || nnz >= (1ll << 31) - 64)
+        return set_error(SPMV_ERR_INVALID_ARG, "m, n and nnz must lie in [0, 2^31 - 64)");
+    if (dtype_size(val_dtype) == 0 || dtype_size(vec_dtype) == 0)
+        return set_error(SPMV_ERR_INVALID_ARG, "unknown dtype");
+    if (!pair_supported(val_dtype, vec_dtype))
+        return set_error(SPMV_ERR_UNSUPPORTED, "supported (values, vectors): (f64,f64) (f32,f32) (bf16,f32) (f16,f32)");
+    if (!ptr) return set_error(SPMV_ERR_INVALID_ARG, "ptr is NULL");
+    if (nnz > 0 && (!idx || !vals)) return set_error(SPMV_ERR_INVALID_ARG, "idx/vals are NULL");
+    if (!aligned16(ptr) || (nnz > 0 && (!aligned16(idx) || !aligned16(vals))))
+        return set_error(SPMV_ERR_INVALID_ARG, "ptr, idx and vals must be 16-byte aligned device pointers");
+    for (const void *q : {(const void *)ptr, (const void *)idx, vals}) {
+        if (q && classify(q) != PK_DEVICE)
+            return set_error(SPMV_ERR_INVALID_ARG, "ptr, idx and vals must be device pointers");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    spmv_plan_s *p = new (std::nothrow) spmv_plan_s();
+    if (!p) return set_error(SPMV_ERR_OOM, "host allocation failed");
+    PlanGuard guard{p};
+    CUDA_TRY(cudaGetDevice(&p->device));
+    p->m = m;
+    p->n = n;
+    p->nnz = nnz;
+    p->layout = layout;
+    p->val_t = val_dtype;
+    p->vec_t = vec_dtype;
+    p->flags = flags;
+    p->n_major = (int)(layout == SPMV_CSC_WIDE ? n : m);
+    p->n_minor = (int)(layout == SPMV_CSC_WIDE ? m : n);
+    p->ptr = ptr;
+    p->idx = idx;
+    p->vals = vals;
+    p->sv = dtype_size(val_dtype);
+    p->sx = dtype_size(vec_dtype);
+    p->sa = (val_dtype == SPMV_F64) ? 8 : 4;
+
+    int sms = 0, smem_max = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    smem_max -= 1024;  // static shared memory and slack
+
+    // ---- launch configuration
+    p->D = (opts && opts->tile_items) ? opts->tile_items : 512;
+    p->S = (opts && opts->stages) ? opts->stages : 3;
+    if (p->D < 64 || p->D > 992 || (p->D % 32) != 0)
+        return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 32 in [64, 992]");
+    if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 8]");
+    p->stage_bytes = (int)align_up((size_t)(p->D + 32) * (4 + std::max(p->sv, p->sx)) + 128, 128);
+    p->table_bytes = (int)align_up((size_t)(p->D + 64) * 4, 128);
+    p->warp_bytes = 256 + p->table_bytes + p->S * p->stage_bytes;
+    const int elem = std::max(p->sa, p->sx);
+    const size_t vec1 = align_up((size_t)p->n_minor * elem, 128);
+    p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) && vec1 + 2 * (size_t)p->warp_bytes <= (size_t)smem_max;
+    const int avail_w = (int)((smem_max - (p->onchip ? vec1 : 0)) / p->warp_bytes);
+    if (avail_w < 1) return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
+    int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 8;
+    W = std::max(1, std::min({W, avail_w, MAX_WARPS}));
+    p->W = W;
+    p->batch_width = 1;
+    if (p->onchip) {
+        for (int kb : {8, 4, 2}) {
+            if (align_up((size_t)p->n_minor * kb * elem, 128) + (size_t)W * p->warp_bytes <= (size_t)smem_max) {
+                p->batch_width = kb;
+                break;
+            }
+        }
+    }
+    if (opts && opts->chunks > 0) {
+        p->P = opts->chunks;
+        p->ctas = (p->P + W - 1) / W;
+    } else {
+        const long items = nnz + p->n_major;
+        const long per_cta = (long)W * p->D * 2;
+        p->ctas = (int)std::max(1L, std::min((long)sms, (items + per_cta - 1) / per_cta));
+        p->P = p->ctas * W;
+    }
+    if (p->P > (1 << 20)) return set_error(SPMV_ERR_INVALID_ARG, "too many chunks");
+
+    // ---- workspace
+    p->pptr_len = (int)align_up((size_t)p->n_major + 1 + 8, 4);
+    const size_t part_bytes = p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
+                                        : (size_t)p->n_minor * sizeof(double);
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_pptr = carve((size_t)p->pptr_len * 4);
+    const size_t o_aux = carve((size_t)p->P * sizeof(ChunkAux));
+    const size_t o_chunks = carve((size_t)p->P * sizeof(ChunkDev));
+    const size_t o_zones = carve((size_t)p->P * sizeof(ZoneDev));
+    const size_t o_counts = carve(16);
+    const size_t o_err = carve(16);
+    const size_t o_recl = carve((size_t)KB_MAX * p->P * sizeof(double));
+    const size_t o_recr = carve((size_t)KB_MAX * p->P * sizeof(double));
+    const size_t o_part = carve(std::max(part_bytes, (size_t)16));
+    p->ws_bytes = off;
+    CUDA_TRY(cudaMalloc(&p->ws, p->ws_bytes));
+    char *w = static_cast<char *>(p->ws);
+    p->pptr = reinterpret_cast<int32_t *>(w + o_pptr);
+    p->aux = reinterpret_cast<ChunkAux *>(w + o_aux);
+    p->chunks = reinterpret_cast<ChunkDev *>(w + o_chunks);
+    p->zones = reinterpret_cast<ZoneDev *>(w + o_zones);
+    p->counts = reinterpret_cast<int32_t *>(w + o_counts);
+    p->err = reinterpret_cast<int32_t *>(w + o_err);
+    p->rec_left = reinterpret_cast<double *>(w + o_recl);
+    p->rec_right = reinterpret_cast<double *>(w + o_recr);
+    p->part = w + o_part;
+    CUDA_TRY(cudaMemsetAsync(p->counts, 0, 32, s));
+    CUDA_TRY(cudaMemsetAsync(p->err, 0, 16, s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)KB_MAX * p->P * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)KB_MAX * p->P * sizeof(double), s));
+
+    // ---- structural checks
+    if (!(flags & SPMV_PLAN_NO_VALIDATE)) {
+        CUDA_TRY(launch_validate(ptr, idx, p->n_major, (int)nnz, p->n_minor, p->err, s));
+        int32_t e = 0;
+        CUDA_TRY(cudaMemcpyAsync(&e, p->err, 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (e) {
+            std::string msg = "malformed matrix:";
+            if (e & 1) msg += " ptr[0] != 0;";
+            if (e & 2) msg += " ptr decreasing or outside [0, nnz];";
+            if (e & 4) msg += " ptr[last] != nnz;";
+            if (e & 8) msg += " index out of range;";
+            return set_error(SPMV_ERR_BAD_MATRIX, msg);
+        }
+    }
+
+    // ---- Sec. II partition and Sec. IV-B set-up on the device
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaEventRecord(e0, s));
+    CUDA_TRY(launch_pad_ptr(ptr, p->pptr, p->n_major, (int)nnz, p->pptr_len, s));
+    CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, p->P, p->D, p->aux, s));
+    CUDA_TRY(launch_setup(p->aux, p->P, p->chunks, p->zones, p->counts, s));
+    int32_t counts[4] = {0, 0, 0, 0};
+    CUDA_TRY(cudaMemcpyAsync(counts, p->counts, 16, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    p->z = counts[0];
+    p->ntiles = counts[1];
+    p->vmax = counts[2];
+    if (p->ntiles > 0) {
+        CUDA_TRY(cudaMalloc(&p->tiles, (size_t)p->ntiles * sizeof(int2)));
+        CUDA_TRY(launch_tiles(p->pptr, p->n_major, p->aux, p->chunks, p->P, p->D, p->ntiles, p->tiles, s));
+    }
+    CUDA_TRY(cudaEventRecord(e1, s));
+    std::vector<ChunkAux> aux(p->P);
+    CUDA_TRY(cudaMemcpyAsync(aux.data(), p->aux, (size_t)p->P * sizeof(ChunkAux), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->setup_ms = ms;
+    p->host_chunks.resize(p->P);
+    p->max_chunk = 0;
+    p->min_chunk = nnz;
+    for (int c = 0; c < p->P; ++c) {
+        const ChunkAux &a = aux[c];
+        spmv_chunk_t &h = p->host_chunks[c];
+        h.nz_begin = a.nz_begin;
+        h.nz_end = a.nz_end;
+        h.jf = a.jf;
+        h.jl = a.jl;
+        h.needLeft = a.needLeft;
+        h.needRight = a.needRight;
+        h.leftGroupEnd = a.leftGroupEnd;
+        h.rightGroup = a.rightGroup;
+        h.leftGroup = a.leftGroup;
+        h.procsOnLeft = a.procsOnLeft;
+        h.procsOnRight = a.procsOnRight;
+        p->max_chunk = std::max<int64_t>(p->max_chunk, a.nz_end - a.nz_begin);
+        p->min_chunk = std::min<int64_t>(p->min_chunk, a.nz_end - a.nz_begin);
+    }
+    guard.p = nullptr;
+    *out = p;
+    return SPMV_OK;
+}
+
+spmv_status spmv_plan_destroy(spmv_plan_t plan) {
+    if (!plan) return SPMV_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return SPMV_OK;
+}
+
+spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
+    if (!p || !info) return set_error(SPMV_ERR_INVALID_ARG, "null argument");
+    std::memset(info, 0, sizeof(*info));
+    info->m = p->m;
+    info->n = p->n;
+    info->nnz = p->nnz;
+    info->layout = p->layout;
+    info->val_dtype = p->val_t;
+    info->vec_dtype = p->vec_t;
+    info->chunks = p->P;
+    info->ctas = p->ctas;
+    info->warps_per_cta = p->W;
+    info->tile_items = p->D;
+    info->stages = p->S;
+    info->tiles = p->ntiles;
+    info->zones = p->z;
+    info->max_zone_size = p->vmax;
+    info->short_on_chip = p->onchip ? 1 : 0;
+    info->batch_width = p->batch_width;
+    info->max_chunk_nnz = p->max_chunk;
+    info->min_chunk_nnz = p->min_chunk;
+    info->imbalance = p->nnz > 0 ? (double)p->P * (double)(p->max_chunk - p->min_chunk) / (double)p->nnz : 0.0;
+    info->workspace_bytes = (int64_t)(p->ws_bytes + (size_t)p->ntiles * sizeof(int2));
+    info->setup_ms = p->setup_ms;
+    return SPMV_OK;
+}
+
+spmv_status spmv_plan_chunks(spmv_plan_t p, spmv_chunk_t *out, int32_t count) {
+    if (!p || !out || count < 0 || count > p->P) return set_error(SPMV_ERR_INVALID_ARG, "bad arguments");
+    std::memcpy(out, p->host_chunks.data(), (size_t)count * sizeof(spmv_chunk_t));
+    return SPMV_OK;
+}
+
+spmv_status spmv(spmv_plan_t p, const void *x, void *y, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return with_staging(p, x, (size_t)p->n * p->sx, y, (size_t)p->m * p->sx, s, [&](const void *dx, void *dy) {
+        return run_op(p, SPMV_OP_AX, 1, &dx, &dy, s);
+    });
+}
+
+spmv_status spvtm(spmv_plan_t p, const void *v, void *u, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    return with_staging(p, v, (size_t)p->m * p->sx, u, (size_t)p->n * p->sx, s, [&](const void *dv, void *du) {
+        return run_op(p, SPMV_OP_VTA, 1, &dv, &du, s);
+    });
+}
+
+spmv_status spmv_batch(spmv_plan_t p, int32_t op, int32_t k, const void *in, int64_t ld_in, void *out, int64_t ld_out,
+                       void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    if (op != SPMV_OP_AX && op != SPMV_OP_VTA) return set_error(SPMV_ERR_INVALID_ARG, "bad op");
+    if (k < 1 || k > 4096) return set_error(SPMV_ERR_INVALID_ARG, "k must lie in [1, 4096]");
+    const int64_t len_in = op == SPMV_OP_AX ? p->n : p->m;
+    const int64_t len_out = op == SPMV_OP_AX ? p->m : p->n;
+    if (ld_in < len_in || ld_out < len_out) return set_error(SPMV_ERR_INVALID_ARG, "ld smaller than vector length");
+    if ((ld_in * p->sx) % 16 || (ld_out * p->sx) % 16)
+        return set_error(SPMV_ERR_INVALID_ARG, "ld * element size must be a multiple of 16 bytes");
+    if (classify(in) != PK_DEVICE || classify(out) != PK_DEVICE || !aligned16(in) || !aligned16(out))
+        return set_error(SPMV_ERR_INVALID_ARG, "spmv_batch takes 16-byte aligned device pointers");
+    std::vector<const void *> vi(k);
+    std::vector<void *> vo(k);
+    for (int b = 0; b < k; ++b) {
+        vi[b] = static_cast<const char *>(in) + (size_t)b * ld_in * p->sx;
+        vo[b] = static_cast<char *>(out) + (size_t)b * ld_out * p->sx;
+    }
+    return run_op(p, op, k, vi.data(), vo.data(), static_cast<cudaStream_t>(stream));
+}
+
+spmv_status spmv_dvalues(spmv_plan_t p, const void *r, const void *x, void *g, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    if (!r || !x || (!g && p->nnz > 0)) return set_error(SPMV_ERR_INVALID_ARG, "null pointer");
+    if (p->nnz == 0) return SPMV_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const PtrKind kr = classify(r), kx = classify(x), kg = classify(g);
+    if (kr == PK_DEVICE && kx == PK_DEVICE && kg == PK_DEVICE) {
+        if (!aligned16(r) || !aligned16(x) || !aligned16(g))
+            return set_error(SPMV_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+        return run_dvalues(p, r, x, g, s);
+    }
+    std::lock_guard<std::mutex> lk(p->host_mu);
+    const size_t cap = (size_t)std::max(p->m, p->n) * p->sx + 16;
+    if (!p->hin) CUDA_TRY(cudaMalloc(&p->hin, cap));
+    if (!p->hout) CUDA_TRY(cudaMalloc(&p->hout, cap));
+    if (!p->hg) CUDA_TRY(cudaMalloc(&p->hg, (size_t)p->nnz * p->sv + 16));
+    const void *dr = r, *dx = x;
+    void *dg = g;
+    if (kr == PK_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(p->hin, r, (size_t)p->m * p->sx, cudaMemcpyHostToDevice, s));
+        dr = p->hin;
+    }
+    if (kx == PK_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(p->hout, x, (size_t)p->n * p->sx, cudaMemcpyHostToDevice, s));
+        dx = p->hout;
+    }
+    if (kg == PK_HOST) dg = p->hg;
+    spmv_status st = run_dvalues(p, dr, dx, dg, s);
+    if (st != SPMV_OK) return st;
+    if (kg == PK_HOST) CUDA_TRY(cudaMemcpyAsync(g, dg, (size_t)p->nnz * p->sv, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+spmv_status spmv_check(spmv_plan_t p, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    CUDA_TRY(cudaGetLastError());
+    int32_t e = 0;
+    CUDA_TRY(cudaMemcpy(&e, p->err, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        CUDA_TRY(cudaMemset(p->err, 0, 4));
+        std::string msg = "device error:";
+        if (e & 1) msg += " index outside the short vector (entry skipped);";
+        if (e & 2) msg += " staging wait timed out;";
+        if (e & 4) msg += " inconsistent tile descriptor;";
+        return set_error(SPMV_ERR_DEVICE, msg);
+    }
+    return SPMV_OK;
+}
+
+spmv_status spmv_profile_read(spmv_plan_t p, int32_t kernel, double *ms, int64_t *launches) {
+    if (!p || kernel < 0 || kernel > 4) return set_error(SPMV_ERR_INVALID_ARG, "bad arguments");
+    CUDA_TRY(cudaDeviceSynchronize());
+    std::lock_guard<std::mutex> lk(p->prof_mu);
+    for (auto &pr : p->prof) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, pr.a, pr.b);
+        p->prof_ms[pr.kernel] += t;
+        p->prof_n[pr.kernel] += 1;
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
+    }
+    p->prof.clear();
+    if (ms) *ms = p->prof_ms[kernel];
+    if (launches) *launches = p->prof_n[kernel];
+    return SPMV_OK;
+}
+
+spmv_status spmv_profile_reset(spmv_plan_t p) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    double d;
+    int64_t n;
+    spmv_profile_read(p, 0, &d, &n);
+    std::lock_guard<std::mutex> lk(p->prof_mu);
+    for (int i = 0; i < 5; ++i) {
+        p->prof_ms[i] = 0;
+        p->prof_n[i] = 0;
+    }
+    return SPMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// The plan object behind spmv_plan_t, shared by the C ABI and the serving runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/spmv_gb300.h"
+#include "internal.h"
+
+struct spmv_plan_s {
+    int device = 0;
+    int64_t m = 0, n = 0, nnz = 0;
+    int layout = 0, val_t = 0, vec_t = 0;
+    uint32_t flags = 0;
+    int n_major = 0, n_minor = 0;
+    const int32_t *ptr = nullptr, *idx = nullptr;
+    const void *vals = nullptr;
+    int sv = 4, sx = 4, sa = 4;
+
+    // launch configuration
+    int P = 0, ctas = 0, W = 0, D = 0, S = 0;
+    int stage_bytes = 0, table_bytes = 0, warp_bytes = 0, pptr_len = 0;
+    bool onchip = false;
+    int batch_width = 1;
+
+    // plan-owned device memory
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int32_t *pptr = nullptr;
+    gbk::ChunkAux *aux = nullptr;
+    gbk::ChunkDev *chunks = nullptr;
+    gbk::ZoneDev *zones = nullptr;
+    int32_t *counts = nullptr;
+    int32_t *err = nullptr;
+    double *rec_left = nullptr, *rec_right = nullptr;
+    void *part = nullptr;
+    int2 *tiles = nullptr;
+    int ntiles = 0, z = 0, vmax = 0;
+    double setup_ms = 0.0;
+    int64_t max_chunk = 0, min_chunk = 0;
+
+    // host copy of the per-chunk set-up values
+    std::vector<spmv_chunk_t> host_chunks;
+
+    // staging buffers for host-pointer calls (allocated on first use)
+    std::mutex host_mu;
+    void *hin = nullptr, *hout = nullptr, *hg = nullptr;
+
+    // kernel timers (SPMV_PLAN_PROFILE)
+    struct Prof {
+        int kernel;
+        cudaEvent_t a, b;
+    };
+    std::mutex prof_mu;
+    std::vector<Prof> prof;
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n[5] = {0, 0, 0, 0, 0};
+};
+
+namespace gbk {
+
+// Internal entry points on device pointers (no host staging).  `in`/`out`
+// hold kb <= plan->batch_width vector pointers (kb == 1 off chip).
+spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s);
+spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s);
+// op product on device vectors, any k (split into passes of batch_width)
+spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *const *out, cudaStream_t s);
+size_t plan_footprint(const spmv_plan_s *p);
+spmv_status set_error(spmv_status st, const std::string &msg);
+
+}  // namespace gbk
