@@ -1,0 +1,374 @@
+"""Benchmark of the wide-CSC SpMV/SpVTM pair on one GB300 (or N replicas).
+
+A step is one SpMV y = A x followed by one SpVTM u^T = v^T A on the
+m=20,000 x n=5,000,000 wide CSC matrix with FP32 values and int32 indices
+(about 200M nonzeros, power-law column degrees, 50 dense columns; generated on
+the device from seed 1) -- the SpMV-SpVTM "wrap" the paper's drivers repeat
+1,000 times (Sec. V).  The default run times 1,000 such steps.
+
+Printed JSON (one line, rank 0):
+  value      algorithmic bytes of the pair / device time per step (GB/s), all ranks
+  roofline   dominant kernel: algorithmic bytes per launch / its CUDA-event time,
+             against the measured HBM copy bandwidth
+  e2e        the same metric through the C ABI with host vectors (copies timed)
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+``--impl reference`` times the FP64 oracle itself (the CPU reference of this
+path) on the same workload, one sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMV/SpVTM GB/s vs 8 TB/s HBM peak; served vectors/s with p50/p99 latency"
+WORKLOAD = "wide_csc_m20000_n5000000_fp32_powerlaw2_50dense"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("stream_kernel.cuh", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1812_00904_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel_name)
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload:
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.t = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.samples.append((time.time(), line.strip()))
+
+        self.t = threading.Thread(target=rd, daemon=True)
+        self.t.start()
+
+    def stop(self, t0, t1):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        window = [s for s in self.samples if t0 - 0.25 <= s[0] <= t1 + 0.25] or self.samples[-3:]
+        for _, line in window:
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pair_bytes(m, n, nnz, sv=4, sx=4, si=4, sp=4):
+    """Algorithmic bytes (wide CSC): SpMV Z(si+sv)+(n+1)sp+n sx+m sx; SpVTM Z(si+sv)+(n+1)sp+m sx+n sx."""
+    spmv_b = nnz * (si + sv) + (n + 1) * sp + n * sx + m * sx
+    spvtm_b = nnz * (si + sv) + (n + 1) * sp + m * sx + n * sx
+    return spmv_b, spvtm_b
+
+
+class OracleSample:
+    """A contiguous column block of A on the host, sized so that one FP64 oracle pair takes about `target_s`."""
+
+    def __init__(self, A, target_s: float):
+        import numpy as np
+
+        import synth
+
+        ptr = A.ptr.cpu().numpy().astype(np.int64)
+        n = A.n
+        cols = max(1, n // 64)
+        while True:
+            z = int(ptr[cols])
+            # widened to FP64 once, outside the timed oracle calls
+            S = synth.SparseMatrix("csc", A.m, cols, ptr[:cols + 1].astype(np.int32), A.idx[:z].cpu().numpy(),
+                                   A.vals[:z].double().cpu().numpy())
+            self.S, self.cols, self.z, self.n, self.m = S, cols, z, n, A.m
+            self.x = synth.uniform_vector(cols, 5).astype(np.float32).astype(np.float64)
+            self.v = synth.uniform_vector(A.m, 6).astype(np.float32).astype(np.float64)
+            dt = self.time_pair()
+            if dt >= target_s / 2 or cols == n:
+                break
+            cols = min(n, int(cols * min(8.0, max(1.5, target_s / max(dt, 1e-4)))))
+        b1, b2 = pair_bytes(A.m, cols, z)
+        self.bytes = b1 + b2
+
+    def time_pair(self) -> float:
+        import oracle
+
+        t0 = time.perf_counter()
+        oracle.spmv(self.S, self.x)
+        oracle.spvtm(self.S, self.v)
+        return time.perf_counter() - t0
+
+    def describe(self, reps: int) -> str:
+        return (f"FP64 oracle SpMV+SpVTM pair on the first {self.cols} of {self.n} columns ({self.z} nonzeros), "
+                f"{reps} pair(s), single thread, host {os.uname().machine}")
+
+
+def cpu_baseline(A, target_s: float):
+    smp = OracleSample(A, target_s / 4)
+    reps = 4
+    t = sum(smp.time_pair() for _ in range(reps)) / reps
+    return {"value": round(smp.bytes / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": smp.describe(reps)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle (plain CPU loops) on the same workload, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import torch
+
+    import synth
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A = synth.wide_fp32_large(1, device=dev)
+    per_step = min(2.0, 150.0 / (args.steps + args.warmup))
+    smp = OracleSample(A, per_step)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = smp.time_pair()
+        if i >= args.warmup:
+            times.append(t)
+    t = statistics.median(times)
+    v = round(smp.bytes / t / 1e9, 3)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * t, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "m": A.m, "n": A.n, "nnz": A.nnz, "step": "one SpMV + one SpVTM",
+                      "sample_columns": smp.cols, "sample_nnz": smp.z},
+           "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                            "sample": smp.describe(args.steps)},
+           "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_1812_00904_gb300 as pkg
+    from paper_1812_00904_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        if args.gpus > 1:
+            raise SystemExit(f"--gpus {args.gpus} needs torchrun with {args.gpus} ranks (WORLD_SIZE={world})")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    A = synth.wide_fp32_large(1, device=dev, scale=args.scale)  # every rank holds its own replica
+    m, n, nnz = A.m, A.n, A.nnz
+    plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=pkg.SPMV_PLAN_PROFILE, warps_per_cta=args.warps,
+                    tile_items=args.tile_items, stages=args.stages)
+    info = plan.info()
+    g = torch.Generator(device=dev)
+    g.manual_seed(11)
+    x = torch.rand(n, generator=g, device=dev) * 2 - 1
+    v = torch.rand(m, generator=g, device=dev) * 2 - 1
+    y = torch.empty(m, device=dev)
+    u = torch.empty(n, device=dev)
+
+    def step():
+        pkg.spmv(plan.handle, x, y, stream)
+        pkg.spvtm(plan.handle, v, u, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check()
+    pkg.spmv_profile_reset(plan.handle)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clocks = sampler.stop(t0, t1)
+    plan.check()
+    kt = {k: pkg.spmv_profile_read(plan.handle, k) for k in range(5)}
+    ms_t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    b_spmv, b_spvtm = pair_bytes(m, n, nnz)
+    total_bytes = (b_spmv + b_spvtm) * args.steps * world
+    value = total_bytes / (ms_max / 1e3) / 1e9
+
+    # roofline of the dominant kernel (chunk scatter = SpMV local, chunk dot = SpVTM local)
+    peak, peak_src = load_peaks()
+    k_scatter = (nnz * 8 + (n + 1) * 4 + n * 4)  # idx + values + pointers + x
+    k_segdot = (nnz * 8 + (n + 1) * 4 + m * 4 + n * 4)  # idx + values + pointers + v + u
+    cand = {"chunk_scatter": (kt[0], k_scatter), "chunk_segdot": (kt[2], k_segdot)}
+    dom = max(cand, key=lambda k: cand[k][0][0])
+    (kms, kl), kbytes = cand[dom]
+    avg_s = kms / max(kl, 1) / 1e3
+    achieved = kbytes / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": ncu_traffic(dom, WORKLOAD) if args.scale == 1.0 else None, "bytes_per_launch": kbytes,
+            "avg_launch_us": round(avg_s * 1e6, 2)}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.skip_e2e:
+        xh = None
+    else:
+        xh = x.cpu().pin_memory()
+        vh = v.cpu().pin_memory()
+        yh = torch.empty(m, pin_memory=True)
+        uh = torch.empty(n, pin_memory=True)
+        e2e_steps = max(5, min(args.steps, 200))
+        for _ in range(2):
+            pkg.spmv(plan.handle, xh, yh, stream)
+            pkg.spvtm(plan.handle, vh, uh, stream)
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pkg.spmv(plan.handle, xh, yh, stream)
+            pkg.spvtm(plan.handle, vh, uh, stream)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - te0) / e2e_steps
+        e2e = {"value": round((b_spmv + b_spvtm) / te / 1e9, 1), "unit": "GB/s",
+               "h2d_bytes_per_step": 4 * (n + m), "d2h_bytes_per_step": 4 * (m + n), "steps": e2e_steps,
+               "ms_per_step": round(te * 1e3, 3), "api": "spmv/spvtm with pinned host vectors"}
+
+    out = None
+    if rank == 0:
+        cpu = None
+        if not args.skip_cpu_baseline and world == 1:
+            cpu = cpu_baseline(A, target_s=args.cpu_seconds)
+        spmv_ms = (kt[0][0] + kt[1][0]) / max(kt[0][1], 1)
+        spvtm_ms = (kt[2][0] + kt[3][0]) / max(kt[2][1], 1)
+        out = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD if args.scale == 1.0 else f"{WORKLOAD}_scale{args.scale}",
+                          "m": m, "n": n, "nnz": nnz, "layout": "csc",
+                          "step": "one SpMV + one SpVTM (Sec. V wrap)", "l2": "inputs larger than L2 (no flush)",
+                          "parallelism": f"replicas x{world}", "chunks": info["chunks"], "ctas": info["ctas"],
+                          "warps_per_cta": info["warps_per_cta"], "tile_items": info["tile_items"],
+                          "stages": info["stages"], "zones": info["zones"]},
+               "gflops": round(2 * 2 * nnz * args.steps * world / (ms_max / 1e3) / 1e9, 1),
+               "frac_of_hbm_peak": round(value / world / peak, 4),
+               "ops": {"spmv_gbs": round(b_spmv / (spmv_ms / 1e3) / 1e9, 1),
+                       "spvtm_gbs": round(b_spvtm / (spvtm_ms / 1e3) / 1e9, 1),
+                       "kernel_ms": {name: round(kt[k][0] / max(kt[k][1], 1), 4) for k, name in
+                                     enumerate(["chunk_scatter", "combine", "chunk_segdot", "zone_fixup", "dvalues"])
+                                     if kt[k][1]}},
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": args.steps * (4 if info["zones"] > 0 else 3),
+               "clocks": clocks}
+        print(json.dumps(out))
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="fraction of the 5M columns (a smaller sample of the same workload, for profiling)")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--warps", type=int, default=0, help="warps (chunks) per CTA; 0 = library default")
+    ap.add_argument("--tile-items", type=int, default=0, help="merge items per staged tile; 0 = library default")
+    ap.add_argument("--stages", type=int, default=0, help="staging buffers per warp; 0 = library default")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -357,9 +357,9 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     if (p->D < 64 || p->D > 992 || (p->D % 32) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 32 in [64, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 8]");
-    p->stage_bytes = (int)align_up((size_t)(p->D + 32) * (4 + std::max(p->sv, p->sx)) + 128, 128);
-    p->table_bytes = (int)align_up((size_t)(p->D + 64) * 4, 128);
-    p->warp_bytes = 256 + p->table_bytes + p->S * p->stage_bytes;
+    p->stage_bytes = (int)align_up((size_t)(p->D + 32) * (4 + std::max(p->sv, p->sx)) + 128 + 64, 128);
+    p->table_bytes = 0;
+    p->warp_bytes = 256 + p->S * p->stage_bytes;
     const int elem = std::max(p->sa, p->sx);
     const size_t vec1 = align_up((size_t)p->n_minor * elem, 128);
     p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) && vec1 + 2 * (size_t)p->warp_bytes <= (size_t)smem_max;

@@ -60,7 +60,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
         if (global_timer_ns() - t0 > limit_ns) return false;
     }
 }
@@ -127,6 +128,43 @@ template <> struct Load4<__half, float> {
         const __half2 b = *reinterpret_cast<const __half2 *>(&q.y);
         const float2 fa = __half22float2(a), fb = __half22float2(b);
         v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+    }
+};
+
+// Load 8 consecutive values at element position p (a multiple of 8).
+template <typename VT, typename AT> struct Load8 {
+    __device__ __forceinline__ static void run(const void *base, int p, AT (&v)[8]) {
+        AT a[4], b[4];
+        Load4<VT, AT>::run(base, p, a);
+        Load4<VT, AT>::run(base, p + 4, b);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[e] = a[e];
+            v[e + 4] = b[e];
+        }
+    }
+};
+template <> struct Load8<__nv_bfloat16, float> {
+    __device__ __forceinline__ static void run(const void *base, int p, float (&v)[8]) {
+        const uint4 q = reinterpret_cast<const uint4 *>(base)[p >> 3];
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[2 * e] = __uint_as_float(w[e] << 16);
+            v[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
+        }
+    }
+};
+template <> struct Load8<__half, float> {
+    __device__ __forceinline__ static void run(const void *base, int p, float (&v)[8]) {
+        const uint4 q = reinterpret_cast<const uint4 *>(base)[p >> 3];
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+            v[2 * e] = f.x;
+            v[2 * e + 1] = f.y;
+        }
     }
 };
 
