@@ -87,6 +87,8 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.P = p->P;
     sp.chunks = p->chunks;
     sp.tiles = p->tiles;
+    sp.masks = p->masks;
+    sp.mwp = p->mwp;
     sp.stage_bytes = p->stage_bytes;
     sp.warp_bytes = p->warp_bytes;
     sp.stages = p->S;
@@ -122,7 +124,7 @@ spmv_status set_error(spmv_status st, const std::string &msg) {
 }
 
 size_t plan_footprint(const spmv_plan_s *p) {
-    return p->ws_bytes + (size_t)p->ntiles * sizeof(int2) + (size_t)p->nnz * (4 + p->sv) +
+    return p->ws_bytes + (size_t)p->ntiles * (sizeof(int4) + (size_t)p->mwp * 4) + (size_t)p->nnz * (4 + p->sv) +
            (size_t)(p->n_major + 1) * 4;
 }
 
@@ -245,6 +247,7 @@ void free_plan(spmv_plan_s *p) {
     }
     if (p->ws) cudaFree(p->ws);
     if (p->tiles) cudaFree(p->tiles);
+    if (p->masks) cudaFree(p->masks);
     if (p->hin) cudaFree(p->hin);
     if (p->hout) cudaFree(p->hout);
     if (p->hg) cudaFree(p->hg);
@@ -352,12 +355,15 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     smem_max -= 1024;  // static shared memory and slack
 
     // ---- launch configuration
-    p->D = (opts && opts->tile_items) ? opts->tile_items : 512;
-    p->S = (opts && opts->stages) ? opts->stages : 3;
+    p->D = (opts && opts->tile_items) ? opts->tile_items : 384;
+    p->S = (opts && opts->stages) ? opts->stages : 2;
     if (p->D < 64 || p->D > 992 || (p->D % 32) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 32 in [64, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 8]");
-    p->stage_bytes = (int)align_up((size_t)(p->D + 32) * (4 + std::max(p->sv, p->sx)) + 128 + 64, 128);
+    // head-mask words per tile: positions [0, D + 24) of the staged nonzero cover, rounded to 16 bytes
+    p->mwp = (int)align_up((size_t)(p->D + 24 + 31) / 32, 4);
+    // stage: 64-byte header, nonzero cover (<= D + 24), mask, pointer or vector window (items <= D + 9)
+    p->stage_bytes = (int)align_up(64 + (size_t)(p->D + 40) * (4 + std::max(p->sv, p->sx)) + (size_t)p->mwp * 4 + 64, 128);
     p->table_bytes = 0;
     p->warp_bytes = 256 + p->S * p->stage_bytes;
     const int elem = std::max(p->sa, p->sx);
@@ -365,7 +371,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) && vec1 + 2 * (size_t)p->warp_bytes <= (size_t)smem_max;
     const int avail_w = (int)((smem_max - (p->onchip ? vec1 : 0)) / p->warp_bytes);
     if (avail_w < 1) return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
-    int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 8;
+    int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 16;
     W = std::max(1, std::min({W, avail_w, MAX_WARPS}));
     p->W = W;
     p->batch_width = 1;
@@ -455,8 +461,10 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->ntiles = counts[1];
     p->vmax = counts[2];
     if (p->ntiles > 0) {
-        CUDA_TRY(cudaMalloc(&p->tiles, (size_t)p->ntiles * sizeof(int2)));
+        CUDA_TRY(cudaMalloc(&p->tiles, (size_t)p->ntiles * sizeof(int4)));
+        CUDA_TRY(cudaMalloc(&p->masks, (size_t)p->ntiles * p->mwp * sizeof(uint32_t)));
         CUDA_TRY(launch_tiles(p->pptr, p->n_major, p->aux, p->chunks, p->P, p->D, p->ntiles, p->tiles, s));
+        CUDA_TRY(launch_masks(p->pptr, p->chunks, p->P, p->ntiles, p->mwp, p->tiles, p->masks, s));
     }
     CUDA_TRY(cudaEventRecord(e1, s));
     std::vector<ChunkAux> aux(p->P);
@@ -521,7 +529,7 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->max_chunk_nnz = p->max_chunk;
     info->min_chunk_nnz = p->min_chunk;
     info->imbalance = p->nnz > 0 ? (double)p->P * (double)(p->max_chunk - p->min_chunk) / (double)p->nnz : 0.0;
-    info->workspace_bytes = (int64_t)(p->ws_bytes + (size_t)p->ntiles * sizeof(int2));
+    info->workspace_bytes = (int64_t)(p->ws_bytes + (size_t)p->ntiles * (sizeof(int4) + (size_t)p->mwp * 4));
     info->setup_ms = p->setup_ms;
     return SPMV_OK;
 }

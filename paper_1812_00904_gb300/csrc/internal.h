@@ -44,7 +44,9 @@ struct StreamParams {
     const int32_t *pptr;   // plan-owned padded copy of the pointer array
     int32_t nnz, n_major, n_minor, P;
     const ChunkDev *chunks;
-    const int2 *tiles;     // tile start (k, i) per tile
+    const int4 *tiles;     // per tile: start (k, i), flags (bit0: an empty segment ends in the tile), 0
+    const uint32_t *masks; // per tile: mwp words of segment-start bits (plan-time), 16-byte aligned blocks
+    int32_t mwp;           // mask words per tile (multiple of 4)
     int32_t stage_bytes, warp_bytes, vec_region_bytes, stages;
     int32_t pptr_len, table_bytes;
     int32_t kb;            // vectors in this pass (<= KB template)
@@ -81,6 +83,8 @@ cudaError_t launch_pad_ptr(const int32_t *ptr, int32_t *pptr, int n_major, int n
 cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, int D, ChunkAux *aux, cudaStream_t s);
 cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s);
 cudaError_t launch_tiles(const int32_t *pptr, int n_major, const ChunkAux *aux, const ChunkDev *chunks, int P, int D,
-                         int ntiles, int2 *tiles, cudaStream_t s);
+                         int ntiles, int4 *tiles, cudaStream_t s);
+cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *chunks, int P, int ntiles, int mwp, int4 *tiles,
+                         uint32_t *masks, cudaStream_t s);
 
 }  // namespace gbk

@@ -256,7 +256,7 @@ cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones,
 // path split), moved back to right before a nonzero at a multiple of 8 so that
 // every staged copy starts on a 16-byte boundary.
 __global__ void tiles_kernel(const int32_t *__restrict__ pptr, int n_major, const ChunkAux *__restrict__ aux,
-                             const ChunkDev *__restrict__ chunks, int P, int D, int ntiles, int2 *__restrict__ tiles) {
+                             const ChunkDev *__restrict__ chunks, int P, int D, int ntiles, int4 *__restrict__ tiles) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntiles) return;
     // chunk owning tile t: the last chunk with tile_begin <= t
@@ -270,7 +270,9 @@ __global__ void tiles_kernel(const int32_t *__restrict__ pptr, int n_major, cons
     }
     const ChunkAux a = aux[lo];
     const int q = t - chunks[lo].tile_begin;
-    int2 out;
+    int4 out;
+    out.z = 0;
+    out.w = 0;
     if (q == 0) {
         out.x = a.nz_begin;
         out.y = a.e_begin;
@@ -296,9 +298,63 @@ __global__ void tiles_kernel(const int32_t *__restrict__ pptr, int n_major, cons
 }
 
 cudaError_t launch_tiles(const int32_t *pptr, int n_major, const ChunkAux *aux, const ChunkDev *chunks, int P, int D,
-                         int ntiles, int2 *tiles, cudaStream_t s) {
+                         int ntiles, int4 *tiles, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     tiles_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(pptr, n_major, aux, chunks, P, D, ntiles, tiles);
+    return cudaGetLastError();
+}
+
+// One warp per tile: the segment-start bits of the tile (bit pos set when a
+// segment j in (i0, i1] starts at nonzero kb0 + pos, pos < k1 - kb0), and flag
+// bit 0 when an empty segment ends inside the tile (then several segments can
+// start at one position and the kernels take their general path).
+__global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *__restrict__ chunks, int P, int ntiles,
+                             int mwp, int4 *__restrict__ tiles, uint32_t *__restrict__ masks) {
+    __shared__ uint32_t sm[8][32];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int t = blockIdx.x * 8 + wib;
+    if (t >= ntiles) return;
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = lo + (hi - lo + 1) / 2;
+        if (chunks[mid].tile_begin <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ChunkDev cd = chunks[lo];
+    const int4 a = tiles[t];
+    int k1, i1;
+    if (t + 1 < cd.tile_end) {
+        const int4 b = tiles[t + 1];
+        k1 = b.x;
+        i1 = b.y;
+    } else {
+        k1 = cd.nz_end;
+        i1 = cd.e_end;
+    }
+    const int kb0 = a.x & ~7;
+    const int rel_hi = k1 - kb0;
+    sm[wib][lane] = 0u;
+    __syncwarp();
+    bool dup = false;
+    for (int j = a.y + 1 + lane; j <= i1; j += 32) {
+        const int pj = pptr[j];
+        const int pos = pj - kb0;
+        if (pos >= 0 && pos < rel_hi && pos < 1024) atomicOr(&sm[wib][pos >> 5], 1u << (pos & 31));
+        if (j < i1 && pptr[j + 1] == pj) dup = true;
+    }
+    dup = __any_sync(0xffffffffu, dup);
+    __syncwarp();
+    if (lane < mwp) masks[(size_t)t * mwp + lane] = sm[wib][lane];
+    if (lane == 0) tiles[t].z = dup ? 1 : 0;
+}
+
+cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *chunks, int P, int ntiles, int mwp, int4 *tiles,
+                         uint32_t *masks, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, chunks, P, ntiles, mwp, tiles, masks);
     return cudaGetLastError();
 }
 

@@ -37,7 +37,9 @@ struct spmv_plan_s {
     int32_t *err = nullptr;
     double *rec_left = nullptr, *rec_right = nullptr;
     void *part = nullptr;
-    int2 *tiles = nullptr;
+    int4 *tiles = nullptr;
+    uint32_t *masks = nullptr;
+    int mwp = 0;
     int ntiles = 0, z = 0, vmax = 0;
     double setup_ms = 0.0;
     int64_t max_chunk = 0, min_chunk = 0;

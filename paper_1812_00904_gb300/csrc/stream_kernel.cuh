@@ -38,29 +38,30 @@ constexpr int STAGE_HDR_BYTES = 64;                  // tile geometry at the sta
 struct Geo {              // 64 bytes, written by the producer into the stage header
     int k0, k1, i0, i1;   // nonzeros [k0, k1), end events [i0, i1)
     int kb0, ncov;        // staged nonzero cover [kb0, kb0 + ncov), kb0 = k0 rounded down to 8
-    int pbase, npc;       // staged pointer cover [pbase, pbase + npc)
+    int flags;            // bit 0: an empty segment ends in the tile (general path)
+    int off_val, off_mask, off_ptr, off_x;  // byte offsets after the header
+    int pbase, npc;       // staged pointer cover [pbase, pbase + npc) (general path only)
     int xbase, nxc;       // staged major-vector cover
-    int off_val, off_ptr, off_x;  // byte offsets after the header
-    int bytes;
-    int win;              // pointer/major windows staged (else read from global memory)
-    int ok;               // descriptor consistent (else refused, error word set)
+    int okwin;            // bit 0: descriptor consistent; bit 1: windows staged (else read from global memory)
 };
 
 template <typename VT, typename XT, int MODE>
-__device__ __forceinline__ Geo make_geo(const StreamParams &p, int2 a, int2 b, int nvec) {
+__device__ __forceinline__ Geo make_geo(const StreamParams &p, int4 a, int2 b, int nvec) {
     Geo g;
     g.k0 = a.x;
     g.i0 = a.y;
+    g.flags = a.z;
     g.k1 = b.x;
     g.i1 = b.y;
     g.kb0 = g.k0 & ~7;
     g.ncov = ((g.k1 + 7) & ~7) - g.kb0;
     g.off_val = g.ncov * 4;
-    g.off_ptr = g.off_val + g.ncov * (int)sizeof(VT);
+    g.off_mask = g.off_val + g.ncov * (int)sizeof(VT);
+    g.off_ptr = g.off_mask + p.mwp * 4;
     g.pbase = g.i0 & ~3;
-    g.npc = ((g.i1 + 1 + 3) & ~3) - g.pbase;
+    g.npc = (g.flags & 1) ? ((g.i1 + 1 + 3) & ~3) - g.pbase : 0;
     g.off_x = g.off_ptr + g.npc * 4;
-    g.bytes = g.off_x;
+    int bytes = g.off_x;
     g.xbase = 0;
     g.nxc = 0;
     if (MODE != MODE_SEGDOT) {
@@ -70,14 +71,14 @@ __device__ __forceinline__ Geo make_geo(const StreamParams &p, int2 a, int2 b, i
             g.xbase = g.i0 & ~(xa - 1);
             g.nxc = ((last + 1 + xa - 1) & ~(xa - 1)) - g.xbase;
         }
-        g.bytes = g.off_x + nvec * g.nxc * (int)sizeof(XT);
+        bytes = g.off_x + nvec * g.nxc * (int)sizeof(XT);
     }
     const int cap = p.stage_bytes - STAGE_HDR_BYTES;
-    g.win = g.bytes <= cap;
     // A descriptor that would overrun the stage or the 1024-position head mask
     // is refused; it cannot occur for a plan built by the set-up kernels.
-    g.ok = g.k1 >= g.k0 && g.i1 >= g.i0 && g.k0 >= 0 && g.k1 <= p.nnz && g.i1 <= p.n_major && g.ncov <= 1024 &&
-           g.off_ptr <= cap;
+    const bool ok = g.k1 >= g.k0 && g.i1 >= g.i0 && g.k0 >= 0 && g.k1 <= p.nnz && g.i1 <= p.n_major &&
+                    g.ncov <= 1024 && g.off_ptr <= cap;
+    g.okwin = (ok ? 1 : 0) | (bytes <= cap ? 2 : 0);
     return g;
 }
 
@@ -162,7 +163,6 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
         const bool needRight = (cd.flags & 2) != 0;
         unsigned char *wbase = smem + p.vec_region_bytes + warp * p.warp_bytes;
         uint64_t *bars = reinterpret_cast<uint64_t *>(wbase);
-        uint32_t *mask = reinterpret_cast<uint32_t *>(wbase + 128);
         unsigned char *stages = wbase + WARP_HDR_BYTES;
         const int S = p.stages;
         const int tb = cd.tile_begin;
@@ -187,18 +187,20 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
 
         // tile descriptors, one per lane, a block of 32 at a time (next block prefetched)
         int bcur = 0;
-        int2 dcur = make_int2(0, 0), dnext = make_int2(0, 0);
-        auto load_block = [&](int blk) -> int2 {
+        int4 dcur = make_int4(0, 0, 0, 0), dnext = make_int4(0, 0, 0, 0);
+        auto load_block = [&](int blk) -> int4 {
             const int q = blk * 32 + lane;
-            return q < nt ? p.tiles[tb + q] : make_int2(cd.nz_end, cd.e_end);
+            return q < nt ? p.tiles[tb + q] : make_int4(cd.nz_end, cd.e_end, 0, 0);
         };
-        // start of chunk-local tile q (q == nt gives the chunk end); q's block is bcur or bcur + 1
-        auto tile_at = [&](int q) -> int2 {
-            const int2 src = ((q >> 5) == bcur) ? dcur : dnext;
-            int2 r;
+        // descriptor of chunk-local tile q (q == nt gives the chunk end); q's block is bcur or bcur + 1
+        auto tile_at = [&](int q) -> int4 {
+            const int4 src = ((q >> 5) == bcur) ? dcur : dnext;
+            int4 r;
             r.x = __shfl_sync(FULL, src.x, q & 31);
             r.y = __shfl_sync(FULL, src.y, q & 31);
-            return (q >= nt) ? make_int2(cd.nz_end, cd.e_end) : r;
+            r.z = __shfl_sync(FULL, src.z, q & 31);
+            r.w = 0;
+            return (q >= nt) ? make_int4(cd.nz_end, cd.e_end, 0, 0) : r;
         };
         // all lanes: geometry of tile q into stage s; lane 0 writes the header and issues the copies
         auto issue = [&](int q, int s) {
@@ -207,29 +209,61 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                 ++bcur;
                 dnext = load_block(bcur + 1);
             }
-            const Geo g = make_geo<VT, XT, MODE>(p, tile_at(q), tile_at(q + 1), nvec);
+            const int4 nx = tile_at(q + 1);
+            const Geo g = make_geo<VT, XT, MODE>(p, tile_at(q), make_int2(nx.x, nx.y), nvec);
             unsigned char *st = stages + s * p.stage_bytes;
-            if (lane == 0) {
-                *reinterpret_cast<Geo *>(st) = g;
-                uint64_t *bar = &bars[s];
-                unsigned char *d = st + STAGE_HDR_BYTES;
-                if (g.ok) {
-                    stage_part(d, p.idx, g.kb0, g.ncov, p.nnz, 4, bar);
-                    stage_part(d + g.off_val, p.vals, g.kb0, g.ncov, p.nnz, (int)sizeof(VT), bar);
-                    if (g.win) {
-                        stage_part(d + g.off_ptr, p.pptr, g.pbase, g.npc, p.pptr_len, 4, bar);
-                        if (MODE != MODE_SEGDOT && g.nxc > 0) {
-                            for (int b = 0; b < nvec; ++b) {
-                                const void *src = (MODE == MODE_DVALUES) ? p.vin[1] : p.vin[b];
-                                stage_part(d + g.off_x + b * g.nxc * (int)sizeof(XT), src, g.xbase, g.nxc, p.n_major,
-                                           (int)sizeof(XT), bar);
-                            }
-                        }
-                    }
-                }
-                // releases the header and any plain stores; the bulk bytes complete the phase
-                mbar_arrive(bar);
+            uint64_t *bar = &bars[s];
+            unsigned char *d = st + STAGE_HDR_BYTES;
+            if (lane == 0) *reinterpret_cast<Geo *>(st) = g;
+            // One staged array per lane, in the same instruction stream: 0 indices, 1 values,
+            // 2 head mask, 3 pointer window, 4.. major-vector windows.  The part below an array's
+            // last 16-byte boundary goes by bulk copy, the rest (at most 15 bytes at the very end
+            // of an array) by plain loads before the arrive that releases them.
+            const bool w = (g.okwin & 2) != 0;
+            const void *src = p.idx;
+            unsigned char *dst = d;
+            int e0 = g.kb0, cnt = g.ncov, len = p.nnz, es = 4;
+            if (lane == 1) {
+                src = p.vals;
+                dst = d + g.off_val;
+                es = (int)sizeof(VT);
+            } else if (lane == 2) {
+                src = p.masks + (size_t)(tb + q) * p.mwp;
+                dst = d + g.off_mask;
+                e0 = 0;
+                cnt = p.mwp;
+                len = p.mwp;
+            } else if (lane == 3) {
+                src = p.pptr;
+                dst = d + g.off_ptr;
+                e0 = g.pbase;
+                cnt = w ? g.npc : 0;
+                len = p.pptr_len;
+            } else if (lane >= 4) {
+                const int b = lane - 4;
+                src = (MODE == MODE_DVALUES) ? p.vin[1] : p.vin[b < KB_MAX ? b : 0];
+                dst = d + g.off_x + b * g.nxc * (int)sizeof(XT);
+                e0 = g.xbase;
+                cnt = (MODE != MODE_SEGDOT && w && b < nvec) ? g.nxc : 0;
+                len = p.n_major;
+                es = (int)sizeof(XT);
             }
+            if (!(g.okwin & 1)) cnt = 0;
+            const int al = 16 / es;
+            const int lim = len & ~(al - 1);
+            const int end = e0 + cnt;
+            const int bend = min(end, lim);
+            const uint32_t bytes = bend > e0 ? static_cast<uint32_t>(bend - e0) * es : 0u;
+            if (cnt > 0 && end > lim) {
+                const int t1 = min(end, len);
+                for (int e = max(e0, lim); e < t1; ++e)
+                    copy_elem(dst + (size_t)(e - e0) * es, static_cast<const unsigned char *>(src) + (size_t)e * es, es);
+            }
+            const uint32_t total = __reduce_add_sync(FULL, bytes);
+            __syncwarp();
+            // releases the header and the plain stores; the bulk bytes complete the phase
+            if (lane == 0) mbar_arrive_expect_tx(bar, total);
+            if (bytes) bulk_g2s(dst, static_cast<const unsigned char *>(src) + (size_t)e0 * es, bytes, bar);
         };
 
         if (nt > 0) {
@@ -264,39 +298,30 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                     break;
                 }
                 const Geo g = *reinterpret_cast<const Geo *>(st);
-                if (g.ok) {
+                if (g.okwin & 1) {
                     const unsigned char *dat = st + STAGE_HDR_BYTES;
                     const int rel_lo = g.k0 - g.kb0;
                     const int rel_hi = g.k1 - g.kb0;
+                    const bool win = (g.okwin & 2) != 0;
+                    const bool dup = (g.flags & 1) != 0;
                     const int32_t *idx_s = reinterpret_cast<const int32_t *>(dat);
                     const unsigned char *val_s = dat + g.off_val;
                     const int32_t *ptr_s = reinterpret_cast<const int32_t *>(dat + g.off_ptr);
                     const XT *x_s = reinterpret_cast<const XT *>(dat + g.off_x);
-                    auto PW = [&](int j) -> int { return g.win ? ptr_s[j - g.pbase] : p.pptr[j]; };
+                    auto PW = [&](int j) -> int { return win ? ptr_s[j - g.pbase] : p.pptr[j]; };
 
-                    // ---- A. segment starts inside the tile -> head bits (positions relative to kb0)
-                    mask[lane] = 0u;
-                    __syncwarp();
-                    bool dup = false;
-                    for (int jb = g.i0 + 1; jb <= g.i1; jb += 32) {
-                        const int j = jb + lane;
-                        if (j <= g.i1) {
-                            const int pj = PW(j);
-                            const int pos = pj - g.kb0;
-                            if (pos >= 0 && pos < rel_hi) atomicOr(&mask[pos >> 5], 1u << (pos & 31));
-                            if (j < g.i1 && PW(j + 1) == pj) {  // empty segment j (its end event is in this tile)
-                                dup = true;
-                                if constexpr (MODE == MODE_SEGDOT) {
+                    // ---- A. segment-start bits of the tile (computed by the plan), one word per lane
+                    const uint32_t mw = lane < p.mwp ? reinterpret_cast<const uint32_t *>(dat + g.off_mask)[lane] : 0u;
+                    if constexpr (MODE == MODE_SEGDOT) {
+                        if (dup) {  // empty segments ending in this tile get u_j = 0
+                            for (int j = g.i0 + 1 + lane; j < g.i1; j += 32)
+                                if (PW(j + 1) == PW(j)) {
 #pragma unroll
                                     for (int b = 0; b < KB; ++b)
                                         if (b < kb) static_cast<XT *>(p.vout[b])[j] = zero_of<XT>();
                                 }
-                            }
                         }
                     }
-                    dup = __any_sync(FULL, dup);
-                    __syncwarp();
-                    const uint32_t mw = mask[lane];
                     int incl = __popc(mw);
 #pragma unroll
                     for (int d = 1; d < 32; d <<= 1) {
@@ -375,8 +400,8 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
 #pragma unroll
                                         for (int b = 0; b < KB; ++b) {
                                             if (b < kb) {
-                                                const XT xv = (FAST || g.win) ? x_s[b * g.nxc + ce - g.xbase]
-                                                                              : static_cast<const XT *>(p.vin[b])[ce];
+                                                                    const XT xv = (FAST || win) ? x_s[b * g.nxc + ce - g.xbase]
+                                                                            : static_cast<const XT *>(p.vin[b])[ce];
                                                 const AT contrib = va[e] * static_cast<AT>(xv);
                                                 if constexpr (SMEMV) {
                                                     atomicAdd(reinterpret_cast<AT *>(smem) + ix[e] * KB + b, contrib);
@@ -395,7 +420,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                                 for (int e = 0; e < 4; ++e) {
                                     if ((vm >> e) & 1u) {
                                         const int ce = FAST ? col[e] : col_search(p0 + e);
-                                        const XT xv = (FAST || g.win) ? x_s[ce - g.xbase]
+                                        const XT xv = (FAST || win) ? x_s[ce - g.xbase]
                                                                       : static_cast<const XT *>(p.vin[1])[ce];
                                         AT mv;
                                         if constexpr (SMEMV) {
@@ -442,12 +467,15 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                                 ix[6] = qb.z;
                                 ix[7] = qb.w;
                                 Load8<VT, AT>::run(val_s, p0, va);
-                                uint32_t bad = 0;
+                                unsigned mx = 0;
 #pragma unroll
-                                for (int e = 0; e < 8; ++e)
-                                    bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
-                                if (bad & vm) {
-                                    atomicOr(p.err, ERR_INDEX);
+                                for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(ix[e]));
+                                if (mx >= n_minor) {  // out-of-range entries are skipped and reported
+                                    uint32_t bad = 0;
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e)
+                                        bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
+                                    if (bad & vm) atomicOr(p.err, ERR_INDEX);
                                     vm &= ~bad;
                                 }
                             }
@@ -490,20 +518,17 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                                     // h = 0 closes the segment open at the lane start; h >= 1 closes the
                                     // one ending at item h-1 (the leading one gets the incoming sum)
                                     const AT lead_add = Tex + (before ? AT(0) : chi[b] + clo[b]);
-                                    AT sv[8];
-                                    sv[0] = lead_add;
-#pragma unroll
-                                    for (int h = 1; h < 8; ++h)
-                                        sv[h] = r[h - 1][b] + ((hb & ((1u << h) - 1u)) == 0u ? lead_add : AT(0));
                                     uint32_t rem = hb;
                                     for (int it = 0; it < nemit; ++it) {
                                         const int h = rem ? __ffs(rem) - 1 : 0;
-                                        AT v = sv[0];
+                                        // r[h-1] (h >= 1), selected without indexing the register array
+                                        AT v = AT(0);
 #pragma unroll
-                                        for (int hh = 1; hh < 8; ++hh) v = (h == hh) ? sv[hh] : v;
+                                        for (int hh = 1; hh < 8; ++hh) v = (h == hh) ? r[hh - 1][b] : v;
+                                        const uint32_t upto = hb & ((1u << h) - 1u);
+                                        if (upto == 0u) v += lead_add;  // the segment started before this lane
                                         if (rem) {
-                                            const int col = FAST ? g.i0 + base + __popc(hb & ((1u << h) - 1u))
-                                                                 : col_search(p0 + h - 1);
+                                            const int col = FAST ? g.i0 + base + __popc(upto) : col_search(p0 + h - 1);
                                             emit(col, b, v);
                                         }
                                         rem &= rem - 1u;
@@ -523,12 +548,12 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                         }
                     };
                     if constexpr (MODE == MODE_SEGDOT) {
-                        if (g.win && !dup)
+                        if (!dup)
                             run_steps8(BoolC<true>{});
                         else
                             run_steps8(BoolC<false>{});
                     } else {
-                        if (g.win && !dup)
+                        if (!dup && win)
                             run_steps(BoolC<true>{});
                         else
                             run_steps(BoolC<false>{});
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                     // ---- C. tile end: a segment whose end event lies in this tile is complete
                     if constexpr (MODE == MODE_SEGDOT) {
                         int col_last = g.i0;
-                        if (rel_hi > rel_lo) col_last = (dup || !g.win) ? col_search(rel_hi - 1) : g.i0 + htotal;
+                        if (rel_hi > rel_lo) col_last = dup ? col_search(rel_hi - 1) : g.i0 + htotal;
                         if (col_last < g.i1) {
                             if (lane == 0)
                                 for (int b = 0; b < kb; ++b) emit(col_last, b, chi[b] + clo[b]);
@@ -551,11 +576,9 @@ __global__ void __launch_bounds__(MAX_WARPS * 32, 1) stream_kernel(const __grid_
                 } else if (lane == 0) {
                     atomicOr(p.err, ERR_STRUCT);
                 }
+                // every lane's reads of this stage are done before its refill is issued
                 __syncwarp();
-                if (q + S < nt) {
-                    if (lane == 0) fence_proxy_async_smem();
-                    issue(q + S, s);
-                }
+                if (q + S < nt) issue(q + S, s);
                 if (++s == S) {
                     s = 0;
                     phase ^= 1u;
