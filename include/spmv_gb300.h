@@ -189,6 +189,27 @@ spmv_status spmv_check(spmv_plan_t plan, void *stream);
 spmv_status spmv_profile_read(spmv_plan_t plan, int32_t kernel, double *ms, int64_t *launches);
 spmv_status spmv_profile_reset(spmv_plan_t plan);
 
+/*
+ * spmv_noalloc -- y = A x for a wide CSC matrix (FP32 values and vectors)
+ * without any device allocation, for callers that may not allocate device
+ * memory when they multiply: code inside a memory pool or runtime that hands
+ * the library only pre-sized buffers.  The paper has no counterpart; this is
+ * a convenience path beside spmv_plan/spmv.
+ *   m, n, nnz, ptr, idx, vals  the CSC matrix (device arrays, conventions above); m <= 49152
+ *   x (n floats), y (m floats)  device vectors; y is overwritten
+ *   stream                      cudaStream_t; the call is asynchronous on it
+ * Scratch: the per-CTA partial vectors live in a 16 MiB array in the
+ * library's static device memory, held by every device that loads the
+ * library until the process exits.  All calls share it, so calls that
+ * overlap on the GPU race and give wrong results; serialize them (one stream,
+ * or events).  The first call on a device resolves the array's device address
+ * (set-up), so make that first call before any stream capture.  Nothing is
+ * allocated; an m above 49152 or a bad size is rejected with
+ * SPMV_ERR_INVALID_ARG before any launch.  Indices outside [0, m) are skipped.
+ */
+spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, const int32_t *idx,
+                         const float *vals, const float *x, float *y, void *stream);
+
 /* Thread-local message for the last failing call of this thread ("" if none). */
 const char *spmv_last_error(void);
 

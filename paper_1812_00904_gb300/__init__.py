@@ -16,7 +16,7 @@ from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, 
 
 __all__ = [
     "spmv_plan", "spmv_plan_ex", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
-    "spmv_batch", "spmv_dvalues", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
+    "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
     "spmv_version", "serve_create", "serve_register", "serve_register_host", "serve_submit", "serve_poll",
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
     "SPMV_CSC_WIDE", "SPMV_CSR_TALL", "SPMV_F64", "SPMV_F32", "SPMV_BF16", "SPMV_F16", "SPMV_OP_AX", "SPMV_OP_VTA",
@@ -121,6 +121,11 @@ def spmv_profile_read(plan, kernel: int):
 
 def spmv_profile_reset(plan):
     _lib.call("spmv_profile_reset", plan)
+
+
+def spmv_noalloc(m, n, nnz, ptr, idx, vals, x, y, stream=None):
+    """y = A x (wide CSC, FP32) with no device allocation: scratch in the library's static device memory."""
+    _lib.call("spmv_noalloc", m, n, nnz, _addr(ptr), _addr(idx), _addr(vals), _addr(x), _addr(y), _stream(stream))
 
 
 def spmv_last_error() -> str:

@@ -86,6 +86,7 @@ SIGNATURES = {
     "spmv_check": (_I32, [_P, _P]),
     "spmv_profile_read": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "spmv_profile_reset": (_I32, [_P]),
+    "spmv_noalloc": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P]),
     "spmv_last_error": (ctypes.c_char_p, []),
     "spmv_version": (ctypes.c_char_p, []),
     "serve_create": (_I32, [ctypes.POINTER(_P), _U64, _I32, _I32]),
