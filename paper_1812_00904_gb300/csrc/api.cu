@@ -84,20 +84,26 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.nnz = (int)p->nnz;
     sp.n_major = p->n_major;
     sp.n_minor = p->n_minor;
-    sp.P = p->P;
-    sp.chunks = p->chunks;
-    sp.tiles = p->tiles;
+    sp.meta = p->meta;
     sp.masks = p->masks;
+    sp.ntiles = p->ntiles;
     sp.mwp = p->mwp;
     sp.stage_bytes = p->stage_bytes;
-    sp.warp_bytes = p->warp_bytes;
     sp.stages = p->S;
-    sp.pptr_len = p->pptr_len;
-    sp.table_bytes = p->table_bytes;
+    sp.x_cap = p->x_cap;
     sp.rec_left = p->rec_left;
     sp.rec_right = p->rec_right;
     sp.err = p->err;
     return sp;
+}
+
+// Launch geometry of one streaming pass: W consumer warps + 1 producer warp per CTA.
+void set_geometry(const spmv_plan_s *p, LaunchArgs &a, size_t vec_elem, int kbt) {
+    a.smemv = p->onchip;
+    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kbt * vec_elem, 128) : 0;
+    a.smem = a.sp.vec_region_bytes + p->smem_base;
+    a.grid = p->ctas;
+    a.block = (p->W + 1) * 32;
 }
 
 enum PtrKind { PK_DEVICE, PK_HOST, PK_BAD };
@@ -124,8 +130,7 @@ spmv_status set_error(spmv_status st, const std::string &msg) {
 }
 
 size_t plan_footprint(const spmv_plan_s *p) {
-    return p->ws_bytes + (size_t)p->ntiles * (sizeof(int4) + (size_t)p->mwp * 4) + (size_t)p->nnz * (4 + p->sv) +
-           (size_t)(p->n_major + 1) * 4;
+    return p->ws_bytes + (size_t)p->nnz * (4 + p->sv) + (size_t)(p->n_major + 1) * 4;
 }
 
 spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
@@ -146,13 +151,9 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     a.sp = base_params(p);
     a.sp.kb = kb;
     for (int b = 0; b < kb; ++b) a.sp.vin[b] = in[b];
-    a.smemv = p->onchip;
-    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kb_template(kb) * p->sa, 128) : 0;
+    set_geometry(p, a, p->sa, kb_template(kb));
     a.sp.part = p->part;
     if (!p->onchip) CUDA_TRY(cudaMemsetAsync(p->part, 0, (size_t)p->n_minor * sizeof(double), s));
-    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
-    a.grid = p->ctas;
-    a.block = p->W * 32;
     a.stream = s;
     {
         ProfScope ps(p, 0, s);
@@ -187,19 +188,15 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
         a.sp.vin[b] = in[b];
         a.sp.vout[b] = out[b];
     }
-    a.smemv = p->onchip;
-    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kb_template(kb) * p->sx, 128) : 0;
-    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
-    a.grid = p->ctas;
-    a.block = p->W * 32;
+    set_geometry(p, a, p->sx, kb_template(kb));
     a.stream = s;
     {
         ProfScope ps(p, 2, s);
         CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
     }
-    if (p->z > 0) {
+    if (p->tz > 0) {
         ProfScope ps(p, 3, s);
-        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, p->zones, p->z, p->rec_left, p->rec_right, p->P, kb, out, s));
+        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, p->tzones, p->tz, p->rec_left, p->rec_right, p->ntiles, kb, out, s));
     }
     return SPMV_OK;
 }
@@ -214,11 +211,7 @@ static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, voi
     a.sp.vin[0] = csc ? r : x;
     a.sp.vin[1] = csc ? x : r;
     a.sp.vout[0] = g;
-    a.smemv = p->onchip;
-    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * p->sx, 128) : 0;
-    a.smem = a.sp.vec_region_bytes + p->W * p->warp_bytes;
-    a.grid = p->ctas;
-    a.block = p->W * 32;
+    set_geometry(p, a, p->sx, 1);
     a.stream = s;
     ProfScope ps(p, 4, s);
     CUDA_TRY(launch_stream(p, MODE_DVALUES, 1, a));
@@ -246,8 +239,7 @@ void free_plan(spmv_plan_s *p) {
         cudaEventDestroy(pr.b);
     }
     if (p->ws) cudaFree(p->ws);
-    if (p->tiles) cudaFree(p->tiles);
-    if (p->masks) cudaFree(p->masks);
+    if (p->ws2) cudaFree(p->ws2);
     if (p->hin) cudaFree(p->hin);
     if (p->hout) cudaFree(p->hout);
     if (p->hg) cudaFree(p->hg);
@@ -354,50 +346,55 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     smem_max -= 1024;  // static shared memory and slack
 
-    // ---- launch configuration
-    p->D = (opts && opts->tile_items) ? opts->tile_items : 384;
-    p->S = (opts && opts->stages) ? opts->stages : 2;
-    if (p->D < 64 || p->D > 992 || (p->D % 32) != 0)
-        return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 32 in [64, 992]");
-    if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 8]");
-    // head-mask words per tile: positions [0, D + 24) of the staged nonzero cover, rounded to 16 bytes
-    p->mwp = (int)align_up((size_t)(p->D + 24 + 31) / 32, 4);
-    // stage: 64-byte header, nonzero cover (<= D + 24), mask, pointer or vector window (items <= D + 9)
-    p->stage_bytes = (int)align_up(64 + (size_t)(p->D + 40) * (4 + std::max(p->sv, p->sx)) + (size_t)p->mwp * 4 + 64, 128);
-    p->table_bytes = 0;
-    p->warp_bytes = 256 + p->S * p->stage_bytes;
-    const int elem = std::max(p->sa, p->sx);
-    const size_t vec1 = align_up((size_t)p->n_minor * elem, 128);
-    p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) && vec1 + 2 * (size_t)p->warp_bytes <= (size_t)smem_max;
-    const int avail_w = (int)((smem_max - (p->onchip ? vec1 : 0)) / p->warp_bytes);
-    if (avail_w < 1) return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
+    // ---- launch configuration: tiles of T nonzeros, rounds of W tiles, S stages per CTA
+    p->T = (opts && opts->tile_items) ? opts->tile_items : 256;
+    p->S = (opts && opts->stages) ? opts->stages : 3;
     int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 16;
-    W = std::max(1, std::min({W, avail_w, MAX_WARPS}));
+    if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)
+        return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
+    if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
+    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 16]");
+    p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
+    const int elem = std::max(p->sa, p->sx);
+    auto stage_for = [&](int w, int bw) {
+        const size_t xcap = align_up((size_t)w * p->T / 4 + 64, 8);
+        return align_up(64 + align_up((size_t)(w + 1) * 16, 16) + ((size_t)w * p->T + 16) * (4 + p->sv) +
+                            (size_t)w * p->mwp * 4 + (size_t)bw * xcap * p->sx,
+                        128);
+    };
+    const size_t vec1 = align_up((size_t)p->n_minor * elem, 128);
+    p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) &&
+                vec1 + 128 + (size_t)p->S * stage_for(std::min(W, 4), 1) <= (size_t)smem_max;
+    const size_t vec_used = p->onchip ? vec1 : 0;
+    while (W > 1 && vec_used + 128 + (size_t)p->S * stage_for(W, 1) > (size_t)smem_max) --W;
+    if (vec_used + 128 + (size_t)p->S * stage_for(W, 1) > (size_t)smem_max)
+        return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
     p->W = W;
     p->batch_width = 1;
     if (p->onchip) {
         for (int kb : {8, 4, 2}) {
-            if (align_up((size_t)p->n_minor * kb * elem, 128) + (size_t)W * p->warp_bytes <= (size_t)smem_max) {
+            if (align_up((size_t)p->n_minor * kb * elem, 128) + 128 + (size_t)p->S * stage_for(W, kb) <=
+                (size_t)smem_max) {
                 p->batch_width = kb;
                 break;
             }
         }
     }
-    if (opts && opts->chunks > 0) {
-        p->P = opts->chunks;
-        p->ctas = (p->P + W - 1) / W;
-    } else {
-        const long items = nnz + p->n_major;
-        const long per_cta = (long)W * p->D * 2;
-        p->ctas = (int)std::max(1L, std::min((long)sms, (items + per_cta - 1) / per_cta));
-        p->P = p->ctas * W;
+    p->x_cap = (int)align_up((size_t)W * p->T / 4 + 64, 8);
+    p->stage_bytes = (int)stage_for(W, p->batch_width);
+    p->smem_base = 128 + p->S * p->stage_bytes;
+    // reporting chunks: the paper's P (default: one per tile)
+    const int64_t P_def = std::max<int64_t>(1, (nnz + p->T - 1) / p->T);
+    p->P = (opts && opts->chunks > 0) ? opts->chunks : (int)P_def;
+    if (p->P > (1 << 24)) return set_error(SPMV_ERR_INVALID_ARG, "too many chunks");
+    {
+        const int64_t q = nnz / p->P;
+        p->max_chunk = q + (nnz % p->P ? 1 : 0);
+        p->min_chunk = q;
     }
-    if (p->P > (1 << 20)) return set_error(SPMV_ERR_INVALID_ARG, "too many chunks");
 
-    // ---- workspace
+    // ---- workspace, part 1: pointer copy, reporting chunks, counters
     p->pptr_len = (int)align_up((size_t)p->n_major + 1 + 8, 4);
-    const size_t part_bytes = p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
-                                        : (size_t)p->n_minor * sizeof(double);
     size_t off = 0;
     auto carve = [&](size_t bytes) {
         const size_t o = off;
@@ -408,27 +405,19 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     const size_t o_aux = carve((size_t)p->P * sizeof(ChunkAux));
     const size_t o_chunks = carve((size_t)p->P * sizeof(ChunkDev));
     const size_t o_zones = carve((size_t)p->P * sizeof(ZoneDev));
-    const size_t o_counts = carve(16);
+    const size_t o_counts = carve(64);
     const size_t o_err = carve(16);
-    const size_t o_recl = carve((size_t)KB_MAX * p->P * sizeof(double));
-    const size_t o_recr = carve((size_t)KB_MAX * p->P * sizeof(double));
-    const size_t o_part = carve(std::max(part_bytes, (size_t)16));
-    p->ws_bytes = off;
-    CUDA_TRY(cudaMalloc(&p->ws, p->ws_bytes));
-    char *w = static_cast<char *>(p->ws);
-    p->pptr = reinterpret_cast<int32_t *>(w + o_pptr);
-    p->aux = reinterpret_cast<ChunkAux *>(w + o_aux);
-    p->chunks = reinterpret_cast<ChunkDev *>(w + o_chunks);
-    p->zones = reinterpret_cast<ZoneDev *>(w + o_zones);
-    p->counts = reinterpret_cast<int32_t *>(w + o_counts);
-    p->err = reinterpret_cast<int32_t *>(w + o_err);
-    p->rec_left = reinterpret_cast<double *>(w + o_recl);
-    p->rec_right = reinterpret_cast<double *>(w + o_recr);
-    p->part = w + o_part;
-    CUDA_TRY(cudaMemsetAsync(p->counts, 0, 32, s));
+    const size_t ws1 = off;
+    CUDA_TRY(cudaMalloc(&p->ws, ws1));
+    char *w1 = static_cast<char *>(p->ws);
+    p->pptr = reinterpret_cast<int32_t *>(w1 + o_pptr);
+    p->aux = reinterpret_cast<ChunkAux *>(w1 + o_aux);
+    p->chunks = reinterpret_cast<ChunkDev *>(w1 + o_chunks);
+    p->zones = reinterpret_cast<ZoneDev *>(w1 + o_zones);
+    p->counts = reinterpret_cast<int32_t *>(w1 + o_counts);
+    p->err = reinterpret_cast<int32_t *>(w1 + o_err);
+    CUDA_TRY(cudaMemsetAsync(p->counts, 0, 64, s));
     CUDA_TRY(cudaMemsetAsync(p->err, 0, 16, s));
-    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)KB_MAX * p->P * sizeof(double), s));
-    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)KB_MAX * p->P * sizeof(double), s));
 
     // ---- structural checks
     if (!(flags & SPMV_PLAN_NO_VALIDATE)) {
@@ -446,13 +435,13 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         }
     }
 
-    // ---- Sec. II partition and Sec. IV-B set-up on the device
+    // ---- Sec. II partition and Sec. IV-B set-up on the device: reporting chunks
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     CUDA_TRY(cudaEventRecord(e0, s));
     CUDA_TRY(launch_pad_ptr(ptr, p->pptr, p->n_major, (int)nnz, p->pptr_len, s));
-    CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, p->P, p->D, p->aux, s));
+    CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, p->P, nullptr, p->T, p->aux, s));
     CUDA_TRY(launch_setup(p->aux, p->P, p->chunks, p->zones, p->counts, s));
     int32_t counts[4] = {0, 0, 0, 0};
     CUDA_TRY(cudaMemcpyAsync(counts, p->counts, 16, cudaMemcpyDeviceToHost, s));
@@ -460,41 +449,60 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->z = counts[0];
     p->ntiles = counts[1];
     p->vmax = counts[2];
-    if (p->ntiles > 0) {
-        CUDA_TRY(cudaMalloc(&p->tiles, (size_t)p->ntiles * sizeof(int4)));
-        CUDA_TRY(cudaMalloc(&p->masks, (size_t)p->ntiles * p->mwp * sizeof(uint32_t)));
-        CUDA_TRY(launch_tiles(p->pptr, p->n_major, p->aux, p->chunks, p->P, p->D, p->ntiles, p->tiles, s));
-        CUDA_TRY(launch_masks(p->pptr, p->chunks, p->P, p->ntiles, p->mwp, p->tiles, p->masks, s));
+    const bool one_tile_each = p->ntiles == p->P;  // every chunk is one tile: reuse its set-up
+
+    // ---- workspace, part 2: tiles (descriptors, masks, zones, records) and partial sums
+    const int nt = p->ntiles;
+    const size_t part_bytes = p->onchip ? (size_t)std::max(1, std::min(sms, nt)) * p->batch_width * p->n_minor * p->sa
+                                        : (size_t)p->n_minor * sizeof(double);
+    off = 0;
+    const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
+    const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
+    const size_t o_tz = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ZoneDev));
+    const size_t o_recl = carve((size_t)p->batch_width * std::max(nt, 1) * sizeof(double));
+    const size_t o_recr = carve((size_t)p->batch_width * std::max(nt, 1) * sizeof(double));
+    const size_t o_part = carve(std::max(part_bytes, (size_t)16));
+    const size_t o_tnzb = carve(one_tile_each ? 16 : (size_t)(nt + 1) * 4);            // set-up only
+    const size_t o_taux = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ChunkAux));
+    const size_t o_tdev = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ChunkDev));
+    const size_t ws2 = off;
+    CUDA_TRY(cudaMalloc(&p->ws2, ws2));
+    p->ws_bytes = ws1 + ws2;
+    char *w2 = static_cast<char *>(p->ws2);
+    p->meta = reinterpret_cast<TileMeta *>(w2 + o_meta);
+    p->masks = reinterpret_cast<uint32_t *>(w2 + o_masks);
+    p->rec_left = reinterpret_cast<double *>(w2 + o_recl);
+    p->rec_right = reinterpret_cast<double *>(w2 + o_recr);
+    p->part = w2 + o_part;
+    ChunkDev *tdev = p->chunks;
+    if (one_tile_each) {
+        p->tzones = p->zones;
+        p->tz = p->z;
+    } else {
+        // cut every chunk into tiles and run the same set-up over the tiles
+        int32_t *tnzb = reinterpret_cast<int32_t *>(w2 + o_tnzb);
+        ChunkAux *taux = reinterpret_cast<ChunkAux *>(w2 + o_taux);
+        tdev = reinterpret_cast<ChunkDev *>(w2 + o_tdev);
+        p->tzones = reinterpret_cast<ZoneDev *>(w2 + o_tz);
+        CUDA_TRY(launch_split(p->chunks, p->P, (int)nnz, nt, tnzb, s));
+        CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, nt, tnzb, p->T, taux, s));
+        CUDA_TRY(launch_setup(taux, nt, tdev, p->tzones, p->counts + 4, s));
+        int32_t tc[4] = {0, 0, 0, 0};
+        CUDA_TRY(cudaMemcpyAsync(tc, p->counts + 4, 16, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        p->tz = tc[0];
     }
+    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)p->batch_width * std::max(nt, 1) * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)p->batch_width * std::max(nt, 1) * sizeof(double), s));
+    CUDA_TRY(launch_masks(p->pptr, tdev, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
+    p->ctas = std::max(1, std::min(sms, nt));
     CUDA_TRY(cudaEventRecord(e1, s));
-    std::vector<ChunkAux> aux(p->P);
-    CUDA_TRY(cudaMemcpyAsync(aux.data(), p->aux, (size_t)p->P * sizeof(ChunkAux), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->setup_ms = ms;
-    p->host_chunks.resize(p->P);
-    p->max_chunk = 0;
-    p->min_chunk = nnz;
-    for (int c = 0; c < p->P; ++c) {
-        const ChunkAux &a = aux[c];
-        spmv_chunk_t &h = p->host_chunks[c];
-        h.nz_begin = a.nz_begin;
-        h.nz_end = a.nz_end;
-        h.jf = a.jf;
-        h.jl = a.jl;
-        h.needLeft = a.needLeft;
-        h.needRight = a.needRight;
-        h.leftGroupEnd = a.leftGroupEnd;
-        h.rightGroup = a.rightGroup;
-        h.leftGroup = a.leftGroup;
-        h.procsOnLeft = a.procsOnLeft;
-        h.procsOnRight = a.procsOnRight;
-        p->max_chunk = std::max<int64_t>(p->max_chunk, a.nz_end - a.nz_begin);
-        p->min_chunk = std::min<int64_t>(p->min_chunk, a.nz_end - a.nz_begin);
-    }
     guard.p = nullptr;
     *out = p;
     return SPMV_OK;
@@ -519,7 +527,7 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->chunks = p->P;
     info->ctas = p->ctas;
     info->warps_per_cta = p->W;
-    info->tile_items = p->D;
+    info->tile_items = p->T;
     info->stages = p->S;
     info->tiles = p->ntiles;
     info->zones = p->z;
@@ -529,14 +537,30 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->max_chunk_nnz = p->max_chunk;
     info->min_chunk_nnz = p->min_chunk;
     info->imbalance = p->nnz > 0 ? (double)p->P * (double)(p->max_chunk - p->min_chunk) / (double)p->nnz : 0.0;
-    info->workspace_bytes = (int64_t)(p->ws_bytes + (size_t)p->ntiles * (sizeof(int4) + (size_t)p->mwp * 4));
+    info->workspace_bytes = (int64_t)p->ws_bytes;
     info->setup_ms = p->setup_ms;
     return SPMV_OK;
 }
 
 spmv_status spmv_plan_chunks(spmv_plan_t p, spmv_chunk_t *out, int32_t count) {
     if (!p || !out || count < 0 || count > p->P) return set_error(SPMV_ERR_INVALID_ARG, "bad arguments");
-    std::memcpy(out, p->host_chunks.data(), (size_t)count * sizeof(spmv_chunk_t));
+    std::vector<ChunkAux> aux((size_t)count);
+    if (count > 0) CUDA_TRY(cudaMemcpy(aux.data(), p->aux, (size_t)count * sizeof(ChunkAux), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < count; ++c) {
+        const ChunkAux &a = aux[c];
+        spmv_chunk_t &h = out[c];
+        h.nz_begin = a.nz_begin;
+        h.nz_end = a.nz_end;
+        h.jf = a.jf;
+        h.jl = a.jl;
+        h.needLeft = a.needLeft;
+        h.needRight = a.needRight;
+        h.leftGroupEnd = a.leftGroupEnd;
+        h.rightGroup = a.rightGroup;
+        h.leftGroup = a.leftGroup;
+        h.procsOnLeft = a.procsOnLeft;
+        h.procsOnRight = a.procsOnRight;
+    }
     return SPMV_OK;
 }
 

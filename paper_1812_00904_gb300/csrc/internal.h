@@ -7,7 +7,7 @@
 
 namespace gbk {
 
-// Kernel modes of the streaming kernel (one staged pass over a chunk's nonzeros).
+// Kernel modes of the streaming kernel (one staged pass over the nonzeros).
 enum Mode : int {
     MODE_SCATTER = 0,  // acc[idx[k]] += val[k] * w[major(k)]   (CSC A x, CSR v^T A)
     MODE_SEGDOT = 1,   // out[j] = sum_{k in segment j} val[k] * w[idx[k]]   (CSC v^T A, CSR A x)
@@ -15,16 +15,16 @@ enum Mode : int {
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
-constexpr int MAX_WARPS = 16;    // warps (chunks) per CTA
-constexpr int MAX_STAGES = 8;
+constexpr int MAX_WARPS = 16;    // consumer warps per CTA (plus one producer warp)
+constexpr int MAX_STAGES = 4;
 
-// Per-chunk descriptor read by the streaming kernels (32 bytes).
+// Per-chunk descriptor produced by the set-up (32 bytes).
 struct ChunkDev {
     int32_t nz_begin, nz_end;   // nonzeros [nz_begin, nz_end) (Sec. II rule)
     int32_t e_begin, e_end;     // segments whose end event the chunk owns: [e_begin, e_end)
     int32_t jf;                 // first segment j^f (-1 if empty)
     int32_t flags;              // bit0 needLeft, bit1 needRight
-    int32_t tile_begin, tile_end;
+    int32_t tile_begin, tile_end;  // execution tiles the chunk is cut into
 };
 
 // Per-chunk quantities of the set-up (Sec. IV-B), device side.
@@ -37,23 +37,30 @@ struct ZoneDev {
     int32_t first, last, col, pad;  // S_k = chunks [first, last], column j_k
 };
 
+// What the streaming kernel reads per execution tile (16 bytes).  Tile t covers
+// nonzeros [meta[t].nzb, meta[t+1].nzb) and owns the segment end events
+// [meta[t].e_begin, meta[t+1].e_begin); meta[ntiles] is the sentinel {nnz, n_major}.
+struct TileMeta {
+    int32_t nzb, e_begin;
+    int32_t flags;  // bit0 needLeft, bit1 needRight, bit2 an empty segment ends in the tile
+    int32_t pad;
+};
+
 // Parameters of the streaming kernel.
 struct StreamParams {
     const int32_t *idx;
     const void *vals;
-    const int32_t *pptr;   // plan-owned padded copy of the pointer array
-    int32_t nnz, n_major, n_minor, P;
-    const ChunkDev *chunks;
-    const int4 *tiles;     // per tile: start (k, i), flags (bit0: an empty segment ends in the tile), 0
-    const uint32_t *masks; // per tile: mwp words of segment-start bits (plan-time), 16-byte aligned blocks
-    int32_t mwp;           // mask words per tile (multiple of 4)
-    int32_t stage_bytes, warp_bytes, vec_region_bytes, stages;
-    int32_t pptr_len, table_bytes;
-    int32_t kb;            // vectors in this pass (<= KB template)
-    const void *vin[KB_MAX];   // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
-    void *vout[KB_MAX];        // SEGDOT: major outputs; DVALUES: vout[0] = g
-    void *part;            // SCATTER: per-CTA partials [cta][kb][n_minor] (on-chip mode) or FP64 accumulator [kb][n_minor]
-    double *rec_left, *rec_right;  // SEGDOT carry records [b * P + c]
+    const int32_t *pptr;     // plan-owned padded copy of the pointer array (general path)
+    int32_t nnz, n_major, n_minor;
+    const TileMeta *meta;    // ntiles + 1 entries
+    const uint32_t *masks;   // per tile: mwp words of segment-start bits
+    int32_t ntiles, mwp;
+    int32_t stage_bytes, vec_region_bytes, stages, x_cap;  // x_cap: window elements per vector
+    int32_t kb;              // vectors in this pass (<= KB template)
+    const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
+    void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g
+    void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
+    double *rec_left, *rec_right;  // SEGDOT carry records [b * ntiles + t]
     int32_t *err;
 };
 
@@ -80,11 +87,15 @@ cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const double
 cudaError_t launch_validate(const int32_t *ptr, const int32_t *idx, int n_major, int nnz, int n_minor, int32_t *err,
                             cudaStream_t s);
 cudaError_t launch_pad_ptr(const int32_t *ptr, int32_t *pptr, int n_major, int nnz, int padded, cudaStream_t s);
-cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, int D, ChunkAux *aux, cudaStream_t s);
+// Per chunk: bounds by the Sec. II rule over P chunks (nzb == nullptr) or from nzb[0..P], first/last
+// segments, owned end events, and the number of execution tiles of at most tmax nonzeros.
+cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, const int32_t *nzb, int tmax, ChunkAux *aux,
+                          cudaStream_t s);
 cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s);
-cudaError_t launch_tiles(const int32_t *pptr, int n_major, const ChunkAux *aux, const ChunkDev *chunks, int P, int D,
-                         int ntiles, int4 *tiles, cudaStream_t s);
-cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *chunks, int P, int ntiles, int mwp, int4 *tiles,
-                         uint32_t *masks, cudaStream_t s);
+// Cut every chunk into its tiles (near-equal pieces): tile_nzb[0..ntiles], sentinel nnz.
+cudaError_t launch_split(const ChunkDev *chunks, int P, int nnz, int ntiles, int32_t *tile_nzb, cudaStream_t s);
+// Per tile: segment-start masks and the kernel's tile descriptors (flags from the tile-level set-up).
+cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles, int nnz, int n_major, int mwp,
+                         uint32_t *masks, TileMeta *meta, cudaStream_t s);
 
 }  // namespace gbk

@@ -59,15 +59,23 @@ __device__ __forceinline__ int ends_upto(const int32_t *pptr, int lo, int hi, lo
     return lo;
 }
 
-// One thread per chunk c: its nonzeros by the Sec. II rule, its first and
-// last segment (j^f, j^l), the segment end events it owns and its tile count.
-__global__ void chunks_kernel(const int32_t *__restrict__ pptr, int n_major, int nnz, int P, int D,
-                              ChunkAux *__restrict__ aux) {
+// One thread per chunk c: its nonzeros (by the Sec. II rule, or from an explicit
+// boundary array), its first and last segment (j^f, j^l), the segment end
+// events it owns, and how many execution tiles of at most tmax nonzeros it is
+// cut into.
+__global__ void chunks_kernel(const int32_t *__restrict__ pptr, int n_major, int nnz, int P,
+                              const int32_t *__restrict__ nzb_arr, int tmax, ChunkAux *__restrict__ aux) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= P) return;
-    const int q = nnz / P, r = nnz % P;
-    const int nzb = c * q + min(c, r);
-    const int nze = nzb + q + (c < r ? 1 : 0);
+    int nzb, nze;
+    if (nzb_arr) {
+        nzb = nzb_arr[c];
+        nze = nzb_arr[c + 1];
+    } else {
+        const int q = nnz / P, r = nnz % P;
+        nzb = c * q + min(c, r);
+        nze = nzb + q + (c < r ? 1 : 0);
+    }
     ChunkAux a;
     a.nz_begin = nzb;
     a.nz_end = nze;
@@ -81,14 +89,15 @@ __global__ void chunks_kernel(const int32_t *__restrict__ pptr, int n_major, int
         a.jf = -1;
         a.jl = -1;
     }
-    const long items = (long)(a.e_end - a.e_begin) + (nze - nzb);
-    a.ntiles = (int)((items + D - 1) / D);
+    a.ntiles = (nze - nzb + tmax - 1) / tmax;
     a.needLeft = a.needRight = a.leftGroupEnd = a.rightGroup = a.leftGroup = a.procsOnLeft = a.procsOnRight = 0;
     aux[c] = a;
 }
 
-cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, int D, ChunkAux *aux, cudaStream_t s) {
-    chunks_kernel<<<(P + 255) / 256, 256, 0, s>>>(pptr, n_major, nnz, P, D, aux);
+cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, const int32_t *nzb, int tmax, ChunkAux *aux,
+                          cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    chunks_kernel<<<(P + 255) / 256, 256, 0, s>>>(pptr, n_major, nnz, P, nzb, tmax, aux);
     return cudaGetLastError();
 }
 
@@ -251,110 +260,77 @@ cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones,
     return cudaGetLastError();
 }
 
-// One thread per tile: the tile starts where the merge order of segment ends
-// and nonzeros reaches the diagonal e_begin + nz_begin + q*D (the classic merge
-// path split), moved back to right before a nonzero at a multiple of 8 so that
-// every staged copy starts on a 16-byte boundary.
-__global__ void tiles_kernel(const int32_t *__restrict__ pptr, int n_major, const ChunkAux *__restrict__ aux,
-                             const ChunkDev *__restrict__ chunks, int P, int D, int ntiles, int4 *__restrict__ tiles) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ntiles) return;
-    // chunk owning tile t: the last chunk with tile_begin <= t
-    int lo = 0, hi = P - 1;
-    while (lo < hi) {
-        const int mid = lo + (hi - lo + 1) / 2;
-        if (chunks[mid].tile_begin <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
+// One thread per chunk: its tiles are near-equal pieces of its nonzeros
+// (the Sec. II rule applied inside the chunk).
+__global__ void split_kernel(const ChunkDev *__restrict__ chunks, int P, int nnz, int ntiles,
+                             int32_t *__restrict__ tile_nzb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= P) return;
+    const ChunkDev d = chunks[c];
+    const int nt = d.tile_end - d.tile_begin;
+    const int len = d.nz_end - d.nz_begin;
+    if (nt > 0) {
+        const int q = len / nt, r = len % nt;
+        for (int i = 0; i < nt; ++i) tile_nzb[d.tile_begin + i] = d.nz_begin + i * q + min(i, r);
     }
-    const ChunkAux a = aux[lo];
-    const int q = t - chunks[lo].tile_begin;
-    int4 out;
-    out.z = 0;
-    out.w = 0;
-    if (q == 0) {
-        out.x = a.nz_begin;
-        out.y = a.e_begin;
-    } else {
-        const long d = (long)a.e_begin + a.nz_begin + (long)q * D;
-        // largest i in [ilo, ihi] with pptr[i] + i <= d
-        int ilo = (int)max((long)a.e_begin, d - a.nz_end);
-        int ihi = (int)min((long)a.e_end, d - a.nz_begin);
-        while (ilo < ihi) {
-            const int mid = ilo + (ihi - ilo + 1) / 2;
-            if ((long)pptr[mid] + mid <= d)
-                ilo = mid;
-            else
-                ihi = mid - 1;
-        }
-        const int k = (int)(d - ilo);
-        const int kk = max(a.nz_begin, k & ~7);
-        int e = ends_upto(pptr, a.e_begin, a.e_end, kk);
-        out.x = kk;
-        out.y = e;
-    }
-    tiles[t] = out;
+    if (c == P - 1) tile_nzb[ntiles] = nnz;
 }
 
-cudaError_t launch_tiles(const int32_t *pptr, int n_major, const ChunkAux *aux, const ChunkDev *chunks, int P, int D,
-                         int ntiles, int4 *tiles, cudaStream_t s) {
-    if (ntiles <= 0) return cudaSuccess;
-    tiles_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(pptr, n_major, aux, chunks, P, D, ntiles, tiles);
+cudaError_t launch_split(const ChunkDev *chunks, int P, int nnz, int ntiles, int32_t *tile_nzb, cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    split_kernel<<<(P + 255) / 256, 256, 0, s>>>(chunks, P, nnz, ntiles, tile_nzb);
     return cudaGetLastError();
 }
 
 // One warp per tile: the segment-start bits of the tile (bit pos set when a
-// segment j in (i0, i1] starts at nonzero kb0 + pos, pos < k1 - kb0), and flag
-// bit 0 when an empty segment ends inside the tile (then several segments can
-// start at one position and the kernels take their general path).
-__global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *__restrict__ chunks, int P, int ntiles,
-                             int mwp, int4 *__restrict__ tiles, uint32_t *__restrict__ masks) {
+// segment j in (i0, i1] starts at nonzero kb0 + pos, pos < nze - kb0, kb0 =
+// nzb rounded down to 8) and the tile descriptor read by the streaming kernel.
+// Flag bit 2 marks a tile in which an empty segment ends (then several
+// segments can start at one position and the kernels take their general path).
+__global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *__restrict__ tiles, int ntiles, int nnz,
+                             int n_major, int mwp, uint32_t *__restrict__ masks, TileMeta *__restrict__ meta) {
     __shared__ uint32_t sm[8][32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int t = blockIdx.x * 8 + wib;
     if (t >= ntiles) return;
-    int lo = 0, hi = P - 1;
-    while (lo < hi) {
-        const int mid = lo + (hi - lo + 1) / 2;
-        if (chunks[mid].tile_begin <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const ChunkDev cd = chunks[lo];
-    const int4 a = tiles[t];
-    int k1, i1;
-    if (t + 1 < cd.tile_end) {
-        const int4 b = tiles[t + 1];
-        k1 = b.x;
-        i1 = b.y;
-    } else {
-        k1 = cd.nz_end;
-        i1 = cd.e_end;
-    }
-    const int kb0 = a.x & ~7;
-    const int rel_hi = k1 - kb0;
+    const ChunkDev d = tiles[t];
+    const int kb0 = d.nz_begin & ~7;
+    const int rel_hi = d.nz_end - kb0;
     sm[wib][lane] = 0u;
     __syncwarp();
     bool dup = false;
-    for (int j = a.y + 1 + lane; j <= i1; j += 32) {
+    for (int j = d.e_begin + 1 + lane; j <= d.e_end; j += 32) {
         const int pj = pptr[j];
         const int pos = pj - kb0;
-        if (pos >= 0 && pos < rel_hi && pos < 1024) atomicOr(&sm[wib][pos >> 5], 1u << (pos & 31));
-        if (j < i1 && pptr[j + 1] == pj) dup = true;
+        if (pos >= 0 && pos < rel_hi && pos < 32 * mwp) atomicOr(&sm[wib][pos >> 5], 1u << (pos & 31));
+        if (j < d.e_end && pptr[j + 1] == pj) dup = true;
     }
     dup = __any_sync(0xffffffffu, dup);
     __syncwarp();
     if (lane < mwp) masks[(size_t)t * mwp + lane] = sm[wib][lane];
-    if (lane == 0) tiles[t].z = dup ? 1 : 0;
+    if (lane == 0) {
+        TileMeta m;
+        m.nzb = d.nz_begin;
+        m.e_begin = d.e_begin;
+        m.flags = (d.flags & 3) | (dup ? 4 : 0);
+        m.pad = 0;
+        meta[t] = m;
+        if (t == ntiles - 1) {
+            TileMeta e;
+            e.nzb = nnz;
+            e.e_begin = n_major;
+            e.flags = 0;
+            e.pad = 0;
+            meta[ntiles] = e;
+        }
+    }
 }
 
-cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *chunks, int P, int ntiles, int mwp, int4 *tiles,
-                         uint32_t *masks, cudaStream_t s) {
+cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles, int nnz, int n_major, int mwp,
+                         uint32_t *masks, TileMeta *meta, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, chunks, P, ntiles, mwp, tiles, masks);
+    masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, tiles, ntiles, nnz, n_major, mwp, masks, meta);
     return cudaGetLastError();
 }
 

@@ -21,31 +21,31 @@ struct spmv_plan_s {
     int sv = 4, sx = 4, sa = 4;
 
     // launch configuration
-    int P = 0, ctas = 0, W = 0, D = 0, S = 0;
-    int stage_bytes = 0, table_bytes = 0, warp_bytes = 0, pptr_len = 0;
+    int P = 0;          // reporting chunks (the paper's P; spmv_plan_chunks)
+    int ntiles = 0;     // execution tiles (every tile a processor of the kernels)
+    int ctas = 0, W = 0, T = 0, S = 0;
+    int stage_bytes = 0, mwp = 0, x_cap = 0, pptr_len = 0, smem_base = 0;
     bool onchip = false;
     int batch_width = 1;
 
     // plan-owned device memory
-    void *ws = nullptr;
+    void *ws = nullptr;     // pointer copy, reporting chunks, counters
+    void *ws2 = nullptr;    // tile descriptors, masks, zones, records, partials
     size_t ws_bytes = 0;
     int32_t *pptr = nullptr;
-    gbk::ChunkAux *aux = nullptr;
+    gbk::ChunkAux *aux = nullptr;          // reporting chunks (P)
     gbk::ChunkDev *chunks = nullptr;
     gbk::ZoneDev *zones = nullptr;
     int32_t *counts = nullptr;
     int32_t *err = nullptr;
+    gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
+    uint32_t *masks = nullptr;
+    gbk::ZoneDev *tzones = nullptr;        // tile-level overlap zones
     double *rec_left = nullptr, *rec_right = nullptr;
     void *part = nullptr;
-    int4 *tiles = nullptr;
-    uint32_t *masks = nullptr;
-    int mwp = 0;
-    int ntiles = 0, z = 0, vmax = 0;
+    int z = 0, vmax = 0, tz = 0;
     double setup_ms = 0.0;
     int64_t max_chunk = 0, min_chunk = 0;
-
-    // host copy of the per-chunk set-up values
-    std::vector<spmv_chunk_t> host_chunks;
 
     // staging buffers for host-pointer calls (allocated on first use)
     std::mutex host_mu;
