@@ -383,9 +383,11 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->x_cap = (int)align_up((size_t)W * p->T / 4 + 64, 8);
     p->stage_bytes = (int)stage_for(W, p->batch_width);
     p->smem_base = 128 + p->S * p->stage_bytes;
-    // reporting chunks: the paper's P (default: one per tile)
-    const int64_t P_def = std::max<int64_t>(1, (nnz + p->T - 1) / p->T);
-    p->P = (opts && opts->chunks > 0) ? opts->chunks : (int)P_def;
+    // reporting chunks: the paper's P (default: one per warp of a full GPU wave); execution
+    // tiles: T consecutive nonzeros each, every tile a processor of the kernels
+    const int64_t nt64 = (nnz + p->T - 1) / p->T;
+    if (nt64 > (1 << 26)) return set_error(SPMV_ERR_INVALID_ARG, "too many tiles");
+    p->P = (opts && opts->chunks > 0) ? opts->chunks : (int)std::max<int64_t>(1, std::min<int64_t>(nt64, (int64_t)sms * 16));
     if (p->P > (1 << 24)) return set_error(SPMV_ERR_INVALID_ARG, "too many chunks");
     {
         const int64_t q = nnz / p->P;
@@ -447,9 +449,8 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     CUDA_TRY(cudaMemcpyAsync(counts, p->counts, 16, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     p->z = counts[0];
-    p->ntiles = counts[1];
     p->vmax = counts[2];
-    const bool one_tile_each = p->ntiles == p->P;  // every chunk is one tile: reuse its set-up
+    p->ntiles = (int)nt64;
 
     // ---- workspace, part 2: tiles (descriptors, masks, zones, records) and partial sums
     const int nt = p->ntiles;
@@ -458,33 +459,30 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
-    const size_t o_tz = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ZoneDev));
-    const size_t o_recl = carve((size_t)p->batch_width * std::max(nt, 1) * sizeof(double));
-    const size_t o_recr = carve((size_t)p->batch_width * std::max(nt, 1) * sizeof(double));
+    const size_t o_tz = carve((size_t)std::max(nt, 1) * sizeof(ZoneDev));
+    const size_t o_recl = carve((size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa);
+    const size_t o_recr = carve((size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa);
     const size_t o_part = carve(std::max(part_bytes, (size_t)16));
-    const size_t o_tnzb = carve(one_tile_each ? 16 : (size_t)(nt + 1) * 4);            // set-up only
-    const size_t o_taux = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ChunkAux));
-    const size_t o_tdev = carve(one_tile_each ? 16 : (size_t)std::max(nt, 1) * sizeof(ChunkDev));
+    const size_t o_tnzb = carve((size_t)(nt + 1) * 4);  // set-up only
+    const size_t o_taux = carve((size_t)std::max(nt, 1) * sizeof(ChunkAux));
+    const size_t o_tdev = carve((size_t)std::max(nt, 1) * sizeof(ChunkDev));
     const size_t ws2 = off;
     CUDA_TRY(cudaMalloc(&p->ws2, ws2));
     p->ws_bytes = ws1 + ws2;
     char *w2 = static_cast<char *>(p->ws2);
     p->meta = reinterpret_cast<TileMeta *>(w2 + o_meta);
     p->masks = reinterpret_cast<uint32_t *>(w2 + o_masks);
-    p->rec_left = reinterpret_cast<double *>(w2 + o_recl);
-    p->rec_right = reinterpret_cast<double *>(w2 + o_recr);
+    p->rec_left = w2 + o_recl;
+    p->rec_right = w2 + o_recr;
     p->part = w2 + o_part;
-    ChunkDev *tdev = p->chunks;
-    if (one_tile_each) {
-        p->tzones = p->zones;
-        p->tz = p->z;
-    } else {
-        // cut every chunk into tiles and run the same set-up over the tiles
-        int32_t *tnzb = reinterpret_cast<int32_t *>(w2 + o_tnzb);
-        ChunkAux *taux = reinterpret_cast<ChunkAux *>(w2 + o_taux);
-        tdev = reinterpret_cast<ChunkDev *>(w2 + o_tdev);
-        p->tzones = reinterpret_cast<ZoneDev *>(w2 + o_tz);
-        CUDA_TRY(launch_split(p->chunks, p->P, (int)nnz, nt, tnzb, s));
+    // the same Sec. IV-B set-up over the execution tiles gives the tile-level overlap zones
+    int32_t *tnzb = reinterpret_cast<int32_t *>(w2 + o_tnzb);
+    ChunkAux *taux = reinterpret_cast<ChunkAux *>(w2 + o_taux);
+    ChunkDev *tdev = reinterpret_cast<ChunkDev *>(w2 + o_tdev);
+    p->tzones = reinterpret_cast<ZoneDev *>(w2 + o_tz);
+    p->tz = 0;
+    if (nt > 0) {
+        CUDA_TRY(launch_tile_bounds(nt, p->T, (int)nnz, tnzb, s));
         CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, nt, tnzb, p->T, taux, s));
         CUDA_TRY(launch_setup(taux, nt, tdev, p->tzones, p->counts + 4, s));
         int32_t tc[4] = {0, 0, 0, 0};
@@ -492,8 +490,8 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         CUDA_TRY(cudaStreamSynchronize(s));
         p->tz = tc[0];
     }
-    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)p->batch_width * std::max(nt, 1) * sizeof(double), s));
-    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)p->batch_width * std::max(nt, 1) * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa, s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa, s));
     CUDA_TRY(launch_masks(p->pptr, tdev, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
     p->ctas = std::max(1, std::min(sms, nt));
     CUDA_TRY(cudaEventRecord(e1, s));

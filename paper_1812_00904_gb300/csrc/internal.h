@@ -60,7 +60,7 @@ struct StreamParams {
     const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
     void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g
     void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
-    double *rec_left, *rec_right;  // SEGDOT carry records [b * ntiles + t]
+    void *rec_left, *rec_right;  // SEGDOT carry records [b * ntiles + t]: (hi, lo) pairs of the accumulation type
     int32_t *err;
 };
 
@@ -80,7 +80,7 @@ cudaError_t launch_stream_f16(int mode, int kb, const LaunchArgs &a);
 // Small kernels (small_kernels.cu).
 cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int nparts, int n_minor, int kb,
                            void *const *out, cudaStream_t s);
-cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const double *rec_left, const double *rec_right,
+cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s);
 
 // Plan kernels (plan.cu).
@@ -92,8 +92,8 @@ cudaError_t launch_pad_ptr(const int32_t *ptr, int32_t *pptr, int n_major, int n
 cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, const int32_t *nzb, int tmax, ChunkAux *aux,
                           cudaStream_t s);
 cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s);
-// Cut every chunk into its tiles (near-equal pieces): tile_nzb[0..ntiles], sentinel nnz.
-cudaError_t launch_split(const ChunkDev *chunks, int P, int nnz, int ntiles, int32_t *tile_nzb, cudaStream_t s);
+// Execution tile boundaries tile_nzb[t] = min(t * T, nnz), t = 0..ntiles.
+cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cudaStream_t s);
 // Per tile: segment-start masks and the kernel's tile descriptors (flags from the tile-level set-up).
 cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles, int nnz, int n_major, int mwp,
                          uint32_t *masks, TileMeta *meta, cudaStream_t s);

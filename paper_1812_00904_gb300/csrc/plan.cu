@@ -260,25 +260,15 @@ cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones,
     return cudaGetLastError();
 }
 
-// One thread per chunk: its tiles are near-equal pieces of its nonzeros
-// (the Sec. II rule applied inside the chunk).
-__global__ void split_kernel(const ChunkDev *__restrict__ chunks, int P, int nnz, int ntiles,
-                             int32_t *__restrict__ tile_nzb) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= P) return;
-    const ChunkDev d = chunks[c];
-    const int nt = d.tile_end - d.tile_begin;
-    const int len = d.nz_end - d.nz_begin;
-    if (nt > 0) {
-        const int q = len / nt, r = len % nt;
-        for (int i = 0; i < nt; ++i) tile_nzb[d.tile_begin + i] = d.nz_begin + i * q + min(i, r);
-    }
-    if (c == P - 1) tile_nzb[ntiles] = nnz;
+// Execution tile boundaries: tile t covers nonzeros [t*T, min((t+1)*T, nnz)), so
+// every tile starts on a multiple of 8 and fills whole steps of the kernels.
+__global__ void tile_bounds_kernel(int ntiles, int T, int nnz, int32_t *__restrict__ tile_nzb) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= ntiles) tile_nzb[t] = (int)min((long)t * T, (long)nnz);
 }
 
-cudaError_t launch_split(const ChunkDev *chunks, int P, int nnz, int ntiles, int32_t *tile_nzb, cudaStream_t s) {
-    if (P <= 0) return cudaSuccess;
-    split_kernel<<<(P + 255) / 256, 256, 0, s>>>(chunks, P, nnz, ntiles, tile_nzb);
+cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cudaStream_t s) {
+    tile_bounds_kernel<<<(ntiles + 1 + 255) / 256, 256, 0, s>>>(ntiles, T, nnz, tile_nzb);
     return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ struct spmv_plan_s {
     gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
     uint32_t *masks = nullptr;
     gbk::ZoneDev *tzones = nullptr;        // tile-level overlap zones
-    double *rec_left = nullptr, *rec_right = nullptr;
+    void *rec_left = nullptr, *rec_right = nullptr;  // (hi, lo) pairs of the accumulation type
     void *part = nullptr;
     int z = 0, vmax = 0, tz = 0;
     double setup_ms = 0.0;

@@ -35,20 +35,37 @@ __global__ void __launch_bounds__(256) combine_kernel(const PT *__restrict__ par
     static_cast<XT *>(out.p[b])[i] = static_cast<XT>((s0 + s1) + (s2 + s3));
 }
 
-// Zone k spans chunks S_k = [first, last]: u_{j_k} = right record of the first
-// chunk + whole-chunk records of the middle chunks + left record of the last.
-template <typename XT>
+// Zone k spans tiles S_k = [first, last]: u_{j_k} = right record of the first
+// tile + whole-tile records of the middle tiles + left record of the last.
+// Records are (hi, lo) pairs of the accumulation type, added with
+// compensated (TwoSum) arithmetic in that type in a fixed order.
+template <typename T> __device__ __forceinline__ void two_sum_add(T &s, T &c, T v) {
+    const T t = s + v;
+    const T bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+}
+
+template <typename XT, typename T, typename RT>
 __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ zones, int z,
-                                                    const double *__restrict__ rec_left,
-                                                    const double *__restrict__ rec_right, int P, int kb, OutPtrs out) {
+                                                    const RT *__restrict__ rec_left, const RT *__restrict__ rec_right,
+                                                    int P, int kb, OutPtrs out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= z) return;
     const ZoneDev zd = zones[k];
     for (int b = 0; b < kb; ++b) {
-        double s = rec_right[(size_t)b * P + zd.first];
-        for (int c = zd.first + 1; c < zd.last; ++c) s += rec_right[(size_t)b * P + c];
-        s += rec_left[(size_t)b * P + zd.last];
-        static_cast<XT *>(out.p[b])[zd.col] = static_cast<XT>(s);
+        const RT *rr = rec_right + (size_t)b * P;
+        const RT f = rr[zd.first];
+        T s = f.x, c = f.y;
+        for (int q = zd.first + 1; q < zd.last; ++q) {
+            const RT m = rr[q];
+            two_sum_add(s, c, m.x);
+            c += m.y;
+        }
+        const RT l = rec_left[(size_t)b * P + zd.last];
+        two_sum_add(s, c, l.x);
+        c += l.y;
+        static_cast<XT *>(out.p[b])[zd.col] = static_cast<XT>(s + c);
     }
 }
 
@@ -68,16 +85,18 @@ cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int np
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const double *rec_left, const double *rec_right,
+cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s) {
     if (z <= 0) return cudaSuccess;
     OutPtrs o;
     for (int b = 0; b < KB_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
     const int grid = (z + 255) / 256;
     if (vec_f64)
-        fixup_kernel<double><<<grid, 256, 0, s>>>(zones, z, rec_left, rec_right, P, kb, o);
+        fixup_kernel<double, double, double2><<<grid, 256, 0, s>>>(zones, z, static_cast<const double2 *>(rec_left),
+                                                           static_cast<const double2 *>(rec_right), P, kb, o);
     else
-        fixup_kernel<float><<<grid, 256, 0, s>>>(zones, z, rec_left, rec_right, P, kb, o);
+        fixup_kernel<float, float, float2><<<grid, 256, 0, s>>>(zones, z, static_cast<const float2 *>(rec_left),
+                                                         static_cast<const float2 *>(rec_right), P, kb, o);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 template <typename XT> __device__ __forceinline__ XT zero_of() { return XT(0); }
 
+// carry records: (hi, lo) of the accumulation type, widened to FP64 by the zone fixup
+template <typename T> struct Pair;
+template <> struct Pair<float> { using type = float2; };
+template <> struct Pair<double> { using type = double2; };
+__device__ __forceinline__ float2 make_pair2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 make_pair2(double a, double b) { return make_double2(a, b); }
+
 template <bool B> struct BoolC {
     static constexpr bool value = B;
 };
@@ -109,7 +116,7 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
         // ================= producer warp =================
         // tile descriptors, a block of 32 per register (one per lane), the next block prefetched
         int bcur = 0;
-        int2 dcur, dnext;
+        int2 dcur = make_int2(0, 0), dnext = make_int2(0, 0);
         auto load_block = [&](int blk) -> int2 {
             const int t = ta + blk * 32 + lane;
             const TileMeta m = p.meta[min(t, p.ntiles)];
@@ -276,9 +283,10 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                 // Emit the finished dot product of segment `col` for vector b (SEGDOT):
                 // the tile's first segment, when it started in the previous tile, goes
                 // to the tile's left carry record (Sec. IV-A), the rest to out.
+                using AT2 = typename Pair<AT>::type;
                 auto emit = [&](int col, int b, AT value) {
                     if (needLeft && col == i0)
-                        p.rec_left[(size_t)b * p.ntiles + t] = static_cast<double>(value);
+                        static_cast<AT2 *>(p.rec_left)[(size_t)b * p.ntiles + t] = make_pair2(value, AT(0));
                     else
                         static_cast<XT *>(p.vout[b])[col] = static_cast<XT>(value);
                 };
@@ -510,8 +518,7 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                             if (col_last < i1)
                                 emit(col_last, b, v);
                             else if (needRight)
-                                p.rec_right[(size_t)b * p.ntiles + t] = static_cast<double>(chi[b]) +
-                                                                        static_cast<double>(clo[b]);
+                                static_cast<AT2 *>(p.rec_right)[(size_t)b * p.ntiles + t] = make_pair2(chi[b], clo[b]);
                         }
                     }
                 } else {
