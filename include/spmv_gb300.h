@@ -14,7 +14,10 @@
  * column boundaries (Sec. II); chunks that share a column (an "overlap zone")
  * combine their partial dot products through per-chunk carry records and a
  * fixed-order reduction (Sec. IV-A), with the zones numbered by the set-up
- * scans of Sec. IV-B.  On the GPU a chunk is the work of one warp.
+ * scans of Sec. IV-B.  On the GPU the same rule is applied twice: the P
+ * reporting chunks (whose set-up quantities spmv_plan_chunks returns) and the
+ * execution tiles of tile_items nonzeros, each tile a processor of the kernels
+ * with its own carry records.
  *
  * Conventions shared by every call
  * --------------------------------
@@ -39,7 +42,8 @@
  *  - No call aborts the process.  Failures return a status; spmv_last_error()
  *    gives a thread-local message.  Kernels never trap: a device-side failure
  *    (an index out of range, a staging wait that timed out) sets an error word
- *    that spmv_check() reports as SPMV_ERR_DEVICE.
+ *    that spmv_check() reports as SPMV_ERR_DEVICE; the outputs of the call that
+ *    set it are unspecified (out-of-range indices are never dereferenced).
  */
 #ifndef SPMV_GB300_H
 #define SPMV_GB300_H
@@ -77,10 +81,11 @@ typedef struct spmv_plan_s *spmv_plan_t;
 
 /* Optional tuning of a plan; zero fields take the defaults. */
 typedef struct {
-    int32_t chunks;        /* P, the number of nonzero chunks (Sec. II); 0 = one per warp of a full GPU wave */
-    int32_t warps_per_cta; /* warps (chunks) per CTA; 0 = chosen from the shared-memory budget */
-    int32_t tile_items;    /* merge items (nonzeros + column ends) per staged tile, 64..992, multiple of 32 */
-    int32_t stages;        /* staging buffers per warp, 2..8 */
+    int32_t chunks;        /* P, the number of reporting chunks (Sec. II); 0 = min(tiles, 16 per SM) */
+    int32_t warps_per_cta; /* consumer warps per CTA, 1..24 (at most 16 run the multi-vector passes);
+                              0 = 16; lowered to fit the shared-memory budget */
+    int32_t tile_items;    /* nonzeros per execution tile, a multiple of 8 in [8, 992]; 0 = 512 */
+    int32_t stages;        /* staging buffers (rounds of warps_per_cta tiles) per CTA, 2..4; 0 = 2 */
 } spmv_plan_opts;
 
 /* Summary of a plan (spmv_plan_info). */
@@ -89,7 +94,7 @@ typedef struct {
     int32_t layout, val_dtype, vec_dtype;
     int32_t chunks;            /* P */
     int32_t ctas, warps_per_cta, tile_items, stages;
-    int32_t tiles;             /* staged tiles over all chunks */
+    int32_t tiles;             /* execution tiles */
     int32_t zones;             /* z, overlap zones (Sec. II), z <= P-1 */
     int32_t max_zone_size;     /* V = max |S_k| (Sec. IV-A) */
     int32_t short_on_chip;     /* 1 if the short vector lives in shared memory */

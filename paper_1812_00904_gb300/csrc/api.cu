@@ -103,7 +103,7 @@ void set_geometry(const spmv_plan_s *p, LaunchArgs &a, size_t vec_elem, int kbt)
     a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kbt * vec_elem, 128) : 0;
     a.smem = a.sp.vec_region_bytes + p->smem_base;
     a.grid = p->ctas;
-    a.block = (p->W + 1) * 32;
+    a.block = (std::min(p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS) + 1) * 32;
 }
 
 enum PtrKind { PK_DEVICE, PK_HOST, PK_BAD };
@@ -347,13 +347,13 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     smem_max -= 1024;  // static shared memory and slack
 
     // ---- launch configuration: tiles of T nonzeros, rounds of W tiles, S stages per CTA
-    p->T = (opts && opts->tile_items) ? opts->tile_items : 256;
-    p->S = (opts && opts->stages) ? opts->stages : 3;
+    p->T = (opts && opts->tile_items) ? opts->tile_items : 512;
+    p->S = (opts && opts->stages) ? opts->stages : 2;
     int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 16;
     if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
-    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 16]");
+    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 24]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
     const int elem = std::max(p->sa, p->sx);
     auto stage_for = [&](int w, int bw) {

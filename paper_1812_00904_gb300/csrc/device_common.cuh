@@ -168,4 +168,61 @@ template <> struct Load8<__half, float> {
     }
 };
 
+// Staggered 8-value loads.  A warp reads 8 consecutive values per lane (32 bytes
+// of 4-byte values); lanes whose bit 2 is set read their two 16-byte halves in the
+// opposite order, so that each 16-byte load instruction of the warp covers every
+// shared-memory bank exactly four times (no two-way bank conflict).  Register e then
+// holds position e ^ (4 * sw), sw = (lane >> 2) & 1.
+__device__ __forceinline__ void stag8_idx(const int32_t *base, int p, int sw, int (&v)[8]) {
+    const int4 *q = reinterpret_cast<const int4 *>(base) + (p >> 2);
+    const int4 a = q[sw], b = q[1 - sw];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+template <typename VT, typename AT> struct Stag8;
+template <> struct Stag8<float, float> {
+    __device__ __forceinline__ static void run(const void *base, int p, int sw, float (&v)[8]) {
+        const float4 *q = reinterpret_cast<const float4 *>(base) + (p >> 2);
+        const float4 a = q[sw], b = q[1 - sw];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+template <> struct Stag8<double, double> {
+    __device__ __forceinline__ static void run(const void *base, int p, int sw, double (&v)[8]) {
+        const double2 *q = reinterpret_cast<const double2 *>(base) + (p >> 1);
+        const double2 a = q[2 * sw], b = q[2 * sw + 1], c = q[2 - 2 * sw], d = q[3 - 2 * sw];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        v[4] = c.x; v[5] = c.y; v[6] = d.x; v[7] = d.y;
+    }
+};
+template <> struct Stag8<__nv_bfloat16, float> {
+    __device__ __forceinline__ static void run(const void *base, int p, int sw, float (&v)[8]) {
+        const uint4 q = reinterpret_cast<const uint4 *>(base)[p >> 3];
+        const unsigned w[4] = {sw ? q.z : q.x, sw ? q.w : q.y, sw ? q.x : q.z, sw ? q.y : q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            v[2 * e] = __uint_as_float(w[e] << 16);
+            v[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
+        }
+    }
+};
+template <> struct Stag8<__half, float> {
+    __device__ __forceinline__ static void run(const void *base, int p, int sw, float (&v)[8]) {
+        const uint4 q = reinterpret_cast<const uint4 *>(base)[p >> 3];
+        const unsigned w[4] = {sw ? q.z : q.x, sw ? q.w : q.y, sw ? q.x : q.z, sw ? q.y : q.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[e]));
+            v[2 * e] = f.x;
+            v[2 * e + 1] = f.y;
+        }
+    }
+};
+
+// Swap the two 4-bit halves of an 8-bit mask when sw is set (position <-> register order).
+__device__ __forceinline__ uint32_t rot4(uint32_t m, int sw) {
+    return sw ? (((m >> 4) | (m << 4)) & 0xFFu) : m;
+}
+
 }  // namespace gbk

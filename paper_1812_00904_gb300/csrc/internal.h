@@ -15,7 +15,8 @@ enum Mode : int {
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
-constexpr int MAX_WARPS = 16;    // consumer warps per CTA (plus one producer warp)
+constexpr int MAX_WARPS = 24;    // consumer warps per CTA (plus one producer warp), one vector per pass
+constexpr int MAX_WARPS_KB = 16; // consumer warps per CTA of the multi-vector passes (more registers per thread)
 constexpr int MAX_STAGES = 4;
 
 // Per-chunk descriptor produced by the set-up (32 bytes).
@@ -40,7 +41,7 @@ struct ZoneDev {
 // What the streaming kernel reads per execution tile (16 bytes).  Tile t covers
 // nonzeros [meta[t].nzb, meta[t+1].nzb) and owns the segment end events
 // [meta[t].e_begin, meta[t+1].e_begin); meta[ntiles] is the sentinel {nnz, n_major}.
-struct TileMeta {
+struct alignas(16) TileMeta {
     int32_t nzb, e_begin;
     int32_t flags;  // bit0 needLeft, bit1 needRight, bit2 an empty segment ends in the tile
     int32_t pad;

@@ -29,7 +29,7 @@ namespace gbk {
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per pipeline wait
 constexpr int STAGE_HDR_BYTES = 64;                  // round geometry at the start of every stage
 
-struct RoundHdr {         // 64 bytes, written by the producer into the stage header
+struct alignas(16) RoundHdr {  // 64 bytes, written by the producer into the stage header
     int t0, ntl;          // tiles [t0, t0 + ntl)
     int kb0, ncov;        // staged nonzero cover [kb0, kb0 + ncov), kb0 a multiple of 8
     int xbase, nxc;       // staged major-vector cover [xbase, xbase + nxc) (per vector)
@@ -67,7 +67,7 @@ template <bool B> struct BoolC {
 };
 
 template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
-__global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
+__global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
     using AT = typename Acc<VT>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -267,6 +267,7 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                 const int off = kb0 - h.kb0;  // a multiple of 8 elements
                 const int rel_lo = me.nzb - kb0;
                 const int rel_hi = nx.nzb - kb0;
+                const bool full = rel_lo == 0 && (rel_hi & 255) == 0;  // whole 256-position steps only
                 const int32_t *idx_s = reinterpret_cast<const int32_t *>(dat + h.off_idx) + off;
                 const unsigned char *val_s = dat + h.off_val + (size_t)off * sizeof(VT);
                 const XT *x_s = reinterpret_cast<const XT *>(dat + h.off_x);
@@ -322,7 +323,7 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                 const int cnt_ex = incl - __popc(mw);
                 const int htotal = __shfl_sync(FULL, incl, 31);
 
-                // ---- 4 consecutive positions per lane, 128 per step (SCATTER, DVALUES)
+                // ---- DVALUES: 4 consecutive positions per lane, 128 per step
                 auto run_steps4 = [&](auto fast_tag) {
                     constexpr bool FAST = decltype(fast_tag)::value;
                     const int nsteps = (rel_hi + 127) >> 7;
@@ -338,24 +339,17 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                         const int hi_cut = min(max(rel_hi - p0, 0), 4);
                         uint32_t vm = ((1u << hi_cut) - 1u) & ~((1u << lo_cut) - 1u);
                         int ix[4] = {0, 0, 0, 0};
-                        AT va[4] = {AT(0), AT(0), AT(0), AT(0)};
                         if (vm) {
                             const int4 qi = reinterpret_cast<const int4 *>(idx_s)[p0 >> 2];
                             ix[0] = qi.x;
                             ix[1] = qi.y;
                             ix[2] = qi.z;
                             ix[3] = qi.w;
-                            Load4<VT, AT>::run(val_s, p0, va);
-                            const unsigned mx = max(max(static_cast<unsigned>(ix[0]), static_cast<unsigned>(ix[1])),
-                                                    max(static_cast<unsigned>(ix[2]), static_cast<unsigned>(ix[3])));
-                            if (mx >= n_minor) {  // out-of-range entries are skipped and reported
-                                uint32_t bad = 0;
+                            uint32_t bad = 0;
 #pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
-                                if (bad & vm) atomicOr(p.err, ERR_INDEX);
-                                vm &= ~bad;
-                            }
+                            for (int e = 0; e < 4; ++e) bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
+                            if (bad & vm) atomicOr(p.err, ERR_INDEX);  // out-of-range entries are skipped
+                            vm &= ~bad;
                         }
                         int cc = i0 + base;
 #pragma unroll
@@ -363,107 +357,197 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                             cc += (hb >> e) & 1u;
                             if ((vm >> e) & 1u) {
                                 const int ce = FAST ? cc : col_search(p0 + e);
-                                if constexpr (MODE == MODE_SCATTER) {
-#pragma unroll
-                                    for (int b = 0; b < KB; ++b) {
-                                        if (b < kb) {
-                                            const XT xv = win ? x_s[b * p.x_cap + ce - h.xbase]
-                                                              : static_cast<const XT *>(p.vin[b])[ce];
-                                            const AT contrib = va[e] * static_cast<AT>(xv);
-                                            if constexpr (SMEMV) {
-                                                atomicAdd(reinterpret_cast<AT *>(smem) + ix[e] * KB + b, contrib);
-                                            } else {
-                                                atomicAdd(static_cast<double *>(p.part) + (size_t)b * p.n_minor + ix[e],
-                                                          static_cast<double>(contrib));
-                                            }
-                                        }
-                                    }
-                                } else {  // MODE_DVALUES
-                                    const XT xv = win ? x_s[ce - h.xbase] : static_cast<const XT *>(p.vin[1])[ce];
-                                    AT mv;
-                                    if constexpr (SMEMV) {
-                                        mv = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e]]);
-                                    } else {
-                                        mv = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[0]) + ix[e]));
-                                    }
-                                    static_cast<VT *>(p.vout[0])[kb0 + p0 + e] =
-                                        from_d<VT>(static_cast<double>(mv * static_cast<AT>(xv)));
+                                const XT xv = win ? x_s[ce - h.xbase] : static_cast<const XT *>(p.vin[1])[ce];
+                                AT mv;
+                                if constexpr (SMEMV) {
+                                    mv = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e]]);
+                                } else {
+                                    mv = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[0]) + ix[e]));
                                 }
+                                static_cast<VT *>(p.vout[0])[kb0 + p0 + e] =
+                                    from_d<VT>(static_cast<double>(mv * static_cast<AT>(xv)));
                             }
                         }
                     }
                 };
 
-                // ---- SEGDOT: 8 consecutive positions per lane, 256 per step
-                auto run_steps8 = [&](auto fast_tag) {
-                    constexpr bool FAST = decltype(fast_tag)::value;
-                    const int nsteps = (rel_hi + 255) >> 8;
-                    for (int stp = 0; stp < nsteps; ++stp) {
-                        const int p0 = (stp << 8) + (lane << 3);
-                        const int sh = (lane & 3) << 3;
-                        const uint32_t mwl = __shfl_sync(FULL, mw, p0 >> 5);
-                        const int cwl = __shfl_sync(FULL, cnt_ex, p0 >> 5);
-                        const uint32_t hb = (mwl >> sh) & 0xFFu;
-                        const int base = cwl + __popc(mwl & ((1u << sh) - 1u));  // heads before p0
+                // Common prologue of the 8-wide steps: lane l takes positions p0 .. p0+7,
+                // p0 = 256 * stp + 8 * l, staged with the staggered loads (register e holds
+                // position e ^ (4 * sw)).  hb: positional segment-start bits of the lane,
+                // base: segment starts of the tile before p0, vm: positional valid bits
+                // (all set on the whole steps of a tile: WHOLE).
+                const int sw = (lane >> 2) & 1;
+                auto step_head = [&](auto full_tag, int stp, int &p0, uint32_t &hb, int &base, uint32_t &vm) {
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    p0 = (stp << 8) + (lane << 3);
+                    const int sh = (lane & 3) << 3;
+                    const uint32_t mwl = __shfl_sync(FULL, mw, p0 >> 5);
+                    const int cwl = __shfl_sync(FULL, cnt_ex, p0 >> 5);
+                    hb = (mwl >> sh) & 0xFFu;
+                    base = cwl + __popc(mwl & ((1u << sh) - 1u));
+                    if constexpr (WHOLE) {
+                        vm = 0xFFu;
+                    } else {
                         const int lo_cut = min(max(rel_lo - p0, 0), 8);
                         const int hi_cut = min(max(rel_hi - p0, 0), 8);
-                        uint32_t vm = ((1u << hi_cut) - 1u) & ~((1u << lo_cut) - 1u);
-                        int ix[8];
-                        AT va[8];
+                        vm = ((1u << hi_cut) - 1u) & ~((1u << lo_cut) - 1u);
+                    }
+                };
+                // indices and values of the lane's 8 positions (register order); returns the
+                // register-order valid bits with out-of-range indices removed (and reported)
+                auto step_load = [&](auto full_tag, int p0, uint32_t vm_r, int (&ix)[8], AT (&va)[8]) -> uint32_t {
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    if (!WHOLE) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             ix[e] = 0;
                             va[e] = AT(0);
                         }
-                        if (vm) {
-                            const int4 qa = reinterpret_cast<const int4 *>(idx_s)[p0 >> 2];
-                            const int4 qb = reinterpret_cast<const int4 *>(idx_s)[(p0 >> 2) + 1];
-                            ix[0] = qa.x;
-                            ix[1] = qa.y;
-                            ix[2] = qa.z;
-                            ix[3] = qa.w;
-                            ix[4] = qb.x;
-                            ix[5] = qb.y;
-                            ix[6] = qb.z;
-                            ix[7] = qb.w;
-                            Load8<VT, AT>::run(val_s, p0, va);
-                            unsigned mx = 0;
+                    }
+                    if (WHOLE || vm_r) {
+                        stag8_idx(idx_s, p0, sw, ix);
+                        Stag8<VT, AT>::run(val_s, p0, sw, va);
+                        unsigned mx = 0;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(ix[e]));
-                            if (mx >= n_minor) {  // out-of-range entries are skipped and reported
-                                uint32_t bad = 0;
+                        for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(ix[e]));
+                        if (mx >= n_minor) {
+                            uint32_t bad = 0;
 #pragma unroll
-                                for (int e = 0; e < 8; ++e)
-                                    bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
-                                if (bad & vm) atomicOr(p.err, ERR_INDEX);
-                                vm &= ~bad;
-                            }
+                            for (int e = 0; e < 8; ++e) bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
+                            if (bad & vm_r) atomicOr(p.err, ERR_INDEX);  // out-of-range entries are skipped
+                            vm_r &= ~bad;
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                if ((bad >> e) & 1u) {
+                                    ix[e] = 0;
+                                    va[e] = AT(0);
+                                }
                         }
-                        // lane-local inclusive prefix, restarted at every head
-                        AT rr[8][KB];
+                    }
+                    return vm_r;
+                };
+
+                // ---- SCATTER: 8 positions per lane, 256 per step
+                auto run_scatter8 = [&](auto fast_tag, auto win_tag, auto full_tag) {
+                    constexpr bool FAST = decltype(fast_tag)::value;
+                    constexpr bool WIN = decltype(win_tag)::value;
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    auto xval = [&](int b, int ce) -> AT {
+                        if constexpr (WIN) {
+                            return static_cast<AT>(x_s[b * p.x_cap + ce - h.xbase]);
+                        } else {
+                            return static_cast<AT>(static_cast<const XT *>(p.vin[b])[ce]);
+                        }
+                    };
+                    auto add = [&](int row, int b, AT contrib) {
+                        if constexpr (SMEMV) {
+                            atomicAdd(reinterpret_cast<AT *>(smem) + row * KB + b, contrib);
+                        } else {
+                            atomicAdd(static_cast<double *>(p.part) + (size_t)b * p.n_minor + row,
+                                      static_cast<double>(contrib));
+                        }
+                    };
+                    const int nsteps = (rel_hi + 255) >> 8;
+                    for (int stp = 0; stp < nsteps; ++stp) {
+                        int p0, base;
+                        uint32_t hb, vm;
+                        step_head(full_tag, stp, p0, hb, base, vm);
+                        int ix[8];
+                        AT va[8];
+                        const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
+                        const uint32_t hb_r = rot4(hb, sw);
+                        if (FAST && __ballot_sync(FULL, hb != 0u) == 0u) {
+                            // no segment starts in this step: every position is in segment i0 + base
+                            AT xv[KB];
+#pragma unroll
+                            for (int b = 0; b < KB; ++b) xv[b] = (b < kb && (WHOLE || vm_r)) ? xval(b, i0 + base) : AT(0);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                if (WHOLE || ((vm_r >> e) & 1u)) {
+#pragma unroll
+                                    for (int b = 0; b < KB; ++b)
+                                        if (b < kb) add(ix[e], b, va[e] * xv[b]);
+                                }
+                            }
+                            continue;
+                        }
+                        // segment of the first position of each register half
+                        const int h4 = __popc(hb & 0xFu);
+                        int cc = i0 + base + (sw ? h4 : 0);
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
+                            if (e == 4) cc = i0 + base + (sw ? 0 : h4);
+                            cc += (hb_r >> e) & 1u;
+                            if (WHOLE || ((vm_r >> e) & 1u)) {
+                                const int ce = FAST ? cc : col_search(p0 + (e ^ (4 * sw)));
 #pragma unroll
-                            for (int b = 0; b < KB; ++b) {
+                                for (int b = 0; b < KB; ++b)
+                                    if (b < kb) add(ix[e], b, va[e] * xval(b, ce));
+                            }
+                        }
+                    }
+                };
+
+                // ---- SEGDOT: 8 positions per lane, 256 per step.  Finished segments are
+                // emitted from a per-lane scratch of the values that close at each position,
+                // kept in this lane's own (already consumed) slots of the staged step.
+                AT *ev_base = (sizeof(AT) == 8) ? reinterpret_cast<AT *>(const_cast<unsigned char *>(val_s))
+                                                : reinterpret_cast<AT *>(const_cast<int32_t *>(idx_s));
+                auto run_segdot8 = [&](auto fast_tag, auto full_tag) {
+                    constexpr bool FAST = decltype(fast_tag)::value;
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    const int nsteps = (rel_hi + 255) >> 8;
+                    for (int stp = 0; stp < nsteps; ++stp) {
+                        int p0, base;
+                        uint32_t hb, vm;
+                        step_head(full_tag, stp, p0, hb, base, vm);
+                        int ix[8];
+                        AT va[8];
+                        const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
+                        // products in register order, then back to position order
+                        AT rr[8][KB];
+#pragma unroll
+                        for (int b = 0; b < KB; ++b) {
+                            AT pr[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
                                 AT w_ = AT(0);
-                                if ((vm >> e) & 1u) {
+                                if (WHOLE || ((vm_r >> e) & 1u)) {
                                     if constexpr (SMEMV) {
                                         w_ = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e] * KB + b]);
                                     } else {
                                         w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + ix[e]));
                                     }
                                 }
-                                const AT pr = va[e] * w_;
-                                rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pr : rr[e > 0 ? e - 1 : 0][b] + pr;
+                                pr[e] = va[e] * w_;
+                            }
+                            // lane-local inclusive prefix in position order, restarted at every head
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const AT pe = sw ? pr[e ^ 4] : pr[e];
+                                rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pe : rr[e > 0 ? e - 1 : 0][b] + pe;
                             }
                         }
-                        // warp segmented scan of the lanes' open sums (the o operator of Sec. IV-B)
                         const unsigned bal = __ballot_sync(FULL, hb != 0u);
+                        if (bal == 0u) {
+                            // no segment starts in this step: add the step total to the open segment
+#pragma unroll
+                            for (int b = 0; b < KB; ++b) {
+                                AT T = rr[7][b];
+#pragma unroll
+                                for (int d = 16; d >= 1; d >>= 1) T += __shfl_xor_sync(FULL, T, d);
+                                const AT s_ = chi[b] + T;  // compensated addition (TwoSum)
+                                const AT bp = s_ - chi[b];
+                                clo[b] += (chi[b] - (s_ - bp)) + (T - bp);
+                                chi[b] = s_;
+                            }
+                            continue;
+                        }
+                        // warp segmented scan of the lanes' open sums (the o operator of Sec. IV-B)
                         const unsigned le = bal & (FULL >> (31 - lane));
                         const int seg_start = le ? (31 - __clz(le)) : 0;
                         const bool before = (bal & ((1u << lane) - 1u)) != 0u;
-                        const int nemit =
-                            bal ? static_cast<int>(__reduce_max_sync(FULL, static_cast<unsigned>(__popc(hb)))) : 0;
+                        AT *ev = ev_base + p0;
 #pragma unroll
                         for (int b = 0; b < KB; ++b) {
                             AT T = rr[7][b];
@@ -474,41 +558,45 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                             }
                             AT Tex = __shfl_up_sync(FULL, T, 1);
                             if (lane == 0) Tex = AT(0);
-                            if (nemit > 0 && b < kb) {
-                                // the segment closed right before item h (h = 0 closes the one open at
-                                // the lane start; h >= 1 the one ending at item h-1)
-                                const AT lead_add = Tex + (before ? AT(0) : chi[b] + clo[b]);
-                                uint32_t rem = hb;
-                                for (int it = 0; it < nemit; ++it) {
-                                    const int hh0 = rem ? __ffs(rem) - 1 : 0;
-                                    AT v = AT(0);  // rr[hh0-1], selected without indexing the register array
+                            if (hb != 0u && b < kb) {
+                                // value closing at position e: the open sum up to e - 1 (0 at e = 0)
+                                if constexpr (sizeof(AT) == 4) {
+                                    const float4 lo = make_float4(0.f, rr[0][b], rr[1][b], rr[2][b]);
+                                    const float4 hi = make_float4(rr[3][b], rr[4][b], rr[5][b], rr[6][b]);
+                                    float4 *q = reinterpret_cast<float4 *>(ev);
+                                    q[sw] = sw ? hi : lo;  // staggered like the loads
+                                    q[sw ^ 1] = sw ? lo : hi;
+                                } else {
 #pragma unroll
-                                    for (int hh = 1; hh < 8; ++hh) v = (hh0 == hh) ? rr[hh - 1][b] : v;
-                                    const uint32_t upto = hb & ((1u << hh0) - 1u);
-                                    if (upto == 0u) v += lead_add;  // the segment started before this lane
-                                    if (rem) emit(FAST ? i0 + base + __popc(upto) : col_search(p0 + hh0 - 1), b, v);
+                                    for (int e = 1; e < 8; ++e) ev[e] = rr[e - 1][b];
+                                }
+                                // the first head closes the segment flowing into the lane
+                                const AT lead = Tex + (before ? AT(0) : chi[b] + clo[b]);
+                                uint32_t rem = hb;
+                                int k = 0;
+                                while (rem) {
+                                    const int e = __ffs(rem) - 1;
+                                    AT v = (e == 0) ? AT(0) : ev[e];
+                                    if (k == 0) v += lead;
+                                    emit(FAST ? i0 + base + k : col_search(p0 + e - 1), b, v);
                                     rem &= rem - 1u;
+                                    ++k;
                                 }
                             }
-                            const AT T31 = __shfl_sync(FULL, T, 31);
-                            if (bal) {
-                                chi[b] = T31;
-                                clo[b] = AT(0);
-                            } else {  // compensated addition (TwoSum) of the step total
-                                const AT s_ = chi[b] + T31;
-                                const AT bp = s_ - chi[b];
-                                clo[b] += (chi[b] - (s_ - bp)) + (T31 - bp);
-                                chi[b] = s_;
-                            }
+                            chi[b] = __shfl_sync(FULL, T, 31);
+                            clo[b] = AT(0);
                         }
                     }
                 };
 
                 if constexpr (MODE == MODE_SEGDOT) {
-                    if (!dup)
-                        run_steps8(BoolC<true>{});
+                    if (dup)
+                        run_segdot8(BoolC<false>{}, BoolC<false>{});
+                    else if (full)
+                        run_segdot8(BoolC<true>{}, BoolC<true>{});
                     else
-                        run_steps8(BoolC<false>{});
+                        run_segdot8(BoolC<true>{}, BoolC<false>{});
+                    fence_proxy_async_smem();  // the scratch writes precede the next bulk copy into this stage
                     // a segment whose end event lies in this tile is complete; the open one
                     // continues in the next tile: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
@@ -520,6 +608,20 @@ __global__ void __launch_bounds__((MAX_WARPS + 1) * 32, 1) stream_kernel(const _
                             else if (needRight)
                                 static_cast<AT2 *>(p.rec_right)[(size_t)b * p.ntiles + t] = make_pair2(chi[b], clo[b]);
                         }
+                    }
+                } else if constexpr (MODE == MODE_SCATTER) {
+                    if (win) {
+                        if (dup)
+                            run_scatter8(BoolC<false>{}, BoolC<true>{}, BoolC<false>{});
+                        else if (full)
+                            run_scatter8(BoolC<true>{}, BoolC<true>{}, BoolC<true>{});
+                        else
+                            run_scatter8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                    } else {
+                        if (dup)
+                            run_scatter8(BoolC<false>{}, BoolC<false>{}, BoolC<false>{});
+                        else
+                            run_scatter8(BoolC<true>{}, BoolC<false>{}, BoolC<false>{});
                     }
                 } else {
                     if (!dup)

@@ -37,6 +37,30 @@ def test_batch_equals_oracle_per_vector(layout, dtype, k):
     assert torch.equal(single, R[k - 1])
 
 
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+def test_batch_on_a_wide_round_plan(layout):
+    """A plan whose single-vector passes run 24 consumer warps per CTA; the multi-vector
+    passes run fewer warps over the same tiles and must give the same sums bit for bit."""
+    m, n = (900, 40_000) if layout == "csc" else (40_000, 900)
+    A = synth.random_matrix(m, n, layout, density=0.004, seed=77)
+    plan, stored = make_plan(A, torch.float32, tile_items=256, stages=2, warps_per_cta=24)
+    assert plan.info()["warps_per_cta"] == 24
+    k = 5
+    X = torch.stack([dev_vec(synth.uniform_vector(n, 100 + b), torch.float32) for b in range(k)])
+    V = torch.stack([dev_vec(synth.uniform_vector(m, 200 + b), torch.float32) for b in range(k)])
+    Y = plan.batch(pkg.SPMV_OP_AX, X)
+    U = plan.batch(pkg.SPMV_OP_VTA, V)
+    plan.check()
+    for b in range(k):
+        xs, vs = host_of(X[b]), host_of(V[b])
+        assert_close(host_of(Y[b]), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, f"Y[{b}]")
+        assert_close(host_of(U[b]), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, f"U[{b}]")
+    if layout == "csc":
+        assert torch.equal(plan.spvtm(V[2]), U[2])
+    else:
+        assert torch.equal(plan.spmv(X[2]), Y[2])
+
+
 def test_batch_leading_dimension_and_off_chip():
     A = synth.random_matrix(3000, 50_000, "csc", density=0.002, seed=3)
     for flags in (0, pkg.SPMV_PLAN_SHORT_IN_GLOBAL):

@@ -116,7 +116,7 @@ def test_setup_and_products_match_oracle(case, P):
     check_products(plan, stored, synth.uniform_vector(A.n, 1), synth.uniform_vector(A.m, 2), 1e-5, f"{case} P={P}")
 
 
-@pytest.mark.parametrize("tile_items,stages,warps", [(64, 2, 1), (128, 4, 3), (992, 2, 4), (256, 3, 16), (40, 4, 7)])
+@pytest.mark.parametrize("tile_items,stages,warps", [(64, 2, 1), (128, 4, 3), (992, 2, 4), (256, 3, 16), (40, 4, 7), (256, 2, 24), (384, 2, 20), (512, 2, 16)])
 def test_tiling_options(tile_items, stages, warps):
     A = synth.random_matrix(700, 30_000, "csc", degrees=np.minimum(np.random.default_rng(1).zipf(1.9, 30_000), 700),
                             seed=9)
@@ -223,6 +223,38 @@ def test_errors_are_reported_not_raised_on_device():
         pkg.spmv(plan.handle, x.data_ptr() + 4, y)
     assert e.value.status == 1
     plan.check()
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+@pytest.mark.parametrize("flags", [0, pkg.SPMV_PLAN_SHORT_IN_GLOBAL])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16], ids=str)
+def test_unvalidated_out_of_range_indices_set_the_device_error(layout, flags, dtype):
+    """With validation skipped, out-of-range indices are never dereferenced: every
+    product runs to completion, spmv_check reports SPMV_ERR_DEVICE, and the next plan
+    on a valid matrix is unaffected."""
+    m, n = (300, 20_000) if layout == "csc" else (20_000, 300)
+    A = synth.random_matrix(m, n, layout, density=0.01, seed=5)
+    t, stored = device_matrix(A, dtype)
+    bidx = t["idx"].clone()
+    n_minor = m if layout == "csc" else n
+    for pos, val in ((3, n_minor + 7), (A.nnz // 2, 1 << 30), (A.nnz - 1, -1)):
+        bidx[pos] = val
+    plan = pkg.Plan(m, n, t["ptr"], bidx, t["vals"], layout=layout, vec_dtype=torch.float32,
+                    flags=flags | pkg.SPMV_PLAN_NO_VALIDATE, tile_items=512, stages=2)
+    x = dev_vec(synth.uniform_vector(n, 1), torch.float32)
+    v = dev_vec(synth.uniform_vector(m, 2), torch.float32)
+    plan.spmv(x)
+    plan.spvtm(v)
+    plan.dvalues(v, x)
+    plan.batch(pkg.SPMV_OP_AX, torch.stack([x, x, x]))
+    plan.batch(pkg.SPMV_OP_VTA, torch.stack([v, v]))
+    torch.cuda.synchronize()
+    with pytest.raises(pkg.SpmvError) as e:
+        plan.check()
+    assert e.value.status == 5
+    plan.close()
+    good, stored = make_plan(A, dtype)
+    check_products(good, stored, synth.uniform_vector(n, 1), synth.uniform_vector(m, 2), 1e-5, "after error")
 
 
 def test_wide_fp64_workload_matches_oracle():
