@@ -427,8 +427,11 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                     return vm_r;
                 };
 
-                // ---- SCATTER: 8 positions per lane, 256 per step
-                auto run_scatter8 = [&](auto fast_tag, auto win_tag, auto full_tag) {
+                // ---- SCATTER: 256 positions per step, lane l taking positions l, l+32, .., l+224.
+                // Consecutive lanes hold consecutive positions, whose rows (sorted within a
+                // column) fall in different shared-memory banks far more often than the rows
+                // of positions 8 apart: fewer conflicted atomic wavefronts.
+                auto run_scatter = [&](auto fast_tag, auto win_tag, auto full_tag) {
                     constexpr bool FAST = decltype(fast_tag)::value;
                     constexpr bool WIN = decltype(win_tag)::value;
                     constexpr bool WHOLE = decltype(full_tag)::value;
@@ -447,42 +450,88 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                                       static_cast<double>(contrib));
                         }
                     };
+                    const uint32_t *mask_s = reinterpret_cast<const uint32_t *>(dat + h.off_mask) + warp * p.mwp;
+                    const VT *vv = reinterpret_cast<const VT *>(val_s);
+                    const uint32_t lane_le = FULL >> (31 - lane);  // bits 0..lane
                     const int nsteps = (rel_hi + 255) >> 8;
                     for (int stp = 0; stp < nsteps; ++stp) {
-                        int p0, base;
-                        uint32_t hb, vm;
-                        step_head(full_tag, stp, p0, hb, base, vm);
-                        int ix[8];
-                        AT va[8];
-                        const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
-                        const uint32_t hb_r = rot4(hb, sw);
-                        if (FAST && __ballot_sync(FULL, hb != 0u) == 0u) {
-                            // no segment starts in this step: every position is in segment i0 + base
-                            AT xv[KB];
+                        const int s0 = stp << 8;
+                        // segment-start words of the step (positions s0 + 32e .. s0 + 32e + 31)
+                        uint32_t w[8];
+                        {
+                            const uint4 qa = reinterpret_cast<const uint4 *>(mask_s)[2 * stp];
+                            const uint4 qb = reinterpret_cast<const uint4 *>(mask_s)[2 * stp + 1];
+                            w[0] = qa.x; w[1] = qa.y; w[2] = qa.z; w[3] = qa.w;
+                            w[4] = qb.x; w[5] = qb.y; w[6] = qb.z; w[7] = qb.w;
+                            if (!WHOLE) {
 #pragma unroll
-                            for (int b = 0; b < KB; ++b) xv[b] = (b < kb && (WHOLE || vm_r)) ? xval(b, i0 + base) : AT(0);
+                                for (int e = 0; e < 8; ++e)
+                                    if ((stp << 3) + e >= p.mwp) w[e] = 0u;
+                            }
+                        }
+                        const int cb = __shfl_sync(FULL, cnt_ex, stp << 3);  // segment starts before the step
+                        // all loads of the step first (independent), then the additions
+                        int row[8];
+                        AT a[8];
+                        uint32_t ok = 0xFFu;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                if (WHOLE || ((vm_r >> e) & 1u)) {
+                        for (int e = 0; e < 8; ++e) {
+                            const int pos = s0 + (e << 5) + lane;
+                            if (WHOLE || (pos >= rel_lo && pos < rel_hi)) {
+                                row[e] = idx_s[pos];
+                                a[e] = to_acc<AT>(vv[pos]);
+                            } else {
+                                row[e] = 0;
+                                a[e] = AT(0);
+                                ok &= ~(1u << e);
+                            }
+                        }
+                        {
+                            unsigned mx = 0;
 #pragma unroll
-                                    for (int b = 0; b < KB; ++b)
-                                        if (b < kb) add(ix[e], b, va[e] * xv[b]);
+                            for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(row[e]));
+                            if (mx >= n_minor) {  // out-of-range entries are skipped and reported
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    if (static_cast<unsigned>(row[e]) >= n_minor) {
+                                        if ((ok >> e) & 1u) atomicOr(p.err, ERR_INDEX);
+                                        ok &= ~(1u << e);
+                                        row[e] = 0;
+                                        a[e] = AT(0);
+                                    }
+                            }
+                        }
+                        if (FAST && (w[0] | w[1] | w[2] | w[3] | w[4] | w[5] | w[6] | w[7]) == 0u) {
+                            // no segment starts in this step: every position is in segment i0 + cb
+#pragma unroll
+                            for (int b = 0; b < KB; ++b) {
+                                if (b < kb) {
+                                    const AT xv = xval(b, i0 + cb);
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e)
+                                        if (WHOLE || ((ok >> e) & 1u)) add(row[e], b, a[e] * xv);
                                 }
                             }
                             continue;
                         }
-                        // segment of the first position of each register half
-                        const int h4 = __popc(hb & 0xFu);
-                        int cc = i0 + base + (sw ? h4 : 0);
+                        int ce[8];
+                        {
+                            int pre = i0 + cb;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            if (e == 4) cc = i0 + base + (sw ? 0 : h4);
-                            cc += (hb_r >> e) & 1u;
-                            if (WHOLE || ((vm_r >> e) & 1u)) {
-                                const int ce = FAST ? cc : col_search(p0 + (e ^ (4 * sw)));
+                            for (int e = 0; e < 8; ++e) {
+                                ce[e] = FAST ? pre + __popc(w[e] & lane_le) : col_search(s0 + (e << 5) + lane);
+                                pre += __popc(w[e]);
+                            }
+                        }
 #pragma unroll
-                                for (int b = 0; b < KB; ++b)
-                                    if (b < kb) add(ix[e], b, va[e] * xval(b, ce));
+                        for (int b = 0; b < KB; ++b) {
+                            if (b < kb) {
+                                AT xv[8];
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) xv[e] = (WHOLE || ((ok >> e) & 1u)) ? xval(b, ce[e]) : AT(0);
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    if (WHOLE || ((ok >> e) & 1u)) add(row[e], b, a[e] * xv[e]);
                             }
                         }
                     }
@@ -493,98 +542,150 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                 // kept in this lane's own (already consumed) slots of the staged step.
                 AT *ev_base = (sizeof(AT) == 8) ? reinterpret_cast<AT *>(const_cast<unsigned char *>(val_s))
                                                 : reinterpret_cast<AT *>(const_cast<int32_t *>(idx_s));
-                auto run_segdot8 = [&](auto fast_tag, auto full_tag) {
+                // front of a step: segment-start bits, loads, products and the lane-local
+                // inclusive prefix rr (position order, restarted at every head)
+                auto seg_front = [&](auto full_tag, int stp, int &p0, uint32_t &hb, int &base, AT (&rr)[8][KB]) {
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    uint32_t vm;
+                    step_head(full_tag, stp, p0, hb, base, vm);
+                    int ix[8];
+                    AT va[8];
+                    const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
+#pragma unroll
+                    for (int b = 0; b < KB; ++b) {
+                        AT pr[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            AT w_ = AT(0);
+                            if (WHOLE || ((vm_r >> e) & 1u)) {
+                                if constexpr (SMEMV) {
+                                    w_ = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e] * KB + b]);
+                                } else {
+                                    w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + ix[e]));
+                                }
+                            }
+                            pr[e] = va[e] * w_;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const AT pe = sw ? pr[e ^ 4] : pr[e];
+                            rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pe : rr[e > 0 ? e - 1 : 0][b] + pe;
+                        }
+                    }
+                };
+                // warp segmented scan of the lanes' open sums (the o operator of Sec. IV-B):
+                // returns the open sum at the end of this lane; Tex: at the end of the previous lane
+                auto seg_scan = [&](unsigned bal, AT t, AT &Tex) -> AT {
+                    const unsigned le = bal & (FULL >> (31 - lane));
+                    const int seg_start = le ? (31 - __clz(le)) : 0;
+                    AT T = t;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const AT v = __shfl_up_sync(FULL, T, d);
+                        if (lane - d >= seg_start && lane >= d) T += v;
+                    }
+                    Tex = __shfl_up_sync(FULL, T, 1);
+                    if (lane == 0) Tex = AT(0);
+                    return T;
+                };
+                // back of a step for vector b: emit the segments closed in this lane, then
+                // carry the open sum at the end of the step (T31) into (chi, clo)
+                auto seg_back = [&](auto fast_tag, int b, unsigned bal, int p0, uint32_t hb, int base,
+                                    const AT (&rr)[8][KB], AT Tex, AT T31) {
                     constexpr bool FAST = decltype(fast_tag)::value;
+                    if (hb != 0u && b < kb) {
+                        AT *ev = ev_base + p0;
+                        // value closing at position e: the open sum up to e - 1 (0 at e = 0)
+                        if constexpr (sizeof(AT) == 4) {
+                            const float4 lo = make_float4(0.f, rr[0][b], rr[1][b], rr[2][b]);
+                            const float4 hi = make_float4(rr[3][b], rr[4][b], rr[5][b], rr[6][b]);
+                            float4 *q = reinterpret_cast<float4 *>(ev);
+                            q[sw] = sw ? hi : lo;  // staggered like the loads
+                            q[sw ^ 1] = sw ? lo : hi;
+                        } else {
+#pragma unroll
+                            for (int e = 1; e < 8; ++e) ev[e] = rr[e - 1][b];
+                        }
+                        // the first head closes the segment flowing into the lane
+                        const bool before = (bal & ((1u << lane) - 1u)) != 0u;
+                        const AT lead = Tex + (before ? AT(0) : chi[b] + clo[b]);
+                        uint32_t rem = hb;
+                        int k = 0;
+                        while (rem) {
+                            const int e = __ffs(rem) - 1;
+                            AT v = (e == 0) ? AT(0) : ev[e];
+                            if (k == 0) v += lead;
+                            emit(FAST ? i0 + base + k : col_search(p0 + e - 1), b, v);
+                            rem &= rem - 1u;
+                            ++k;
+                        }
+                    }
+                    if (bal) {
+                        chi[b] = T31;
+                        clo[b] = AT(0);
+                    } else {  // compensated addition (TwoSum) of the step total
+                        const AT s_ = chi[b] + T31;
+                        const AT bp = s_ - chi[b];
+                        clo[b] += (chi[b] - (s_ - bp)) + (T31 - bp);
+                        chi[b] = s_;
+                    }
+                };
+                // the open segment runs through a whole head-free step (or pair): add its total
+                auto seg_carry_total = [&](int b, AT t) {
+#pragma unroll
+                    for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
+                    const AT s_ = chi[b] + t;
+                    const AT bp = s_ - chi[b];
+                    clo[b] += (chi[b] - (s_ - bp)) + (t - bp);
+                    chi[b] = s_;
+                };
+                auto run_segdot8 = [&](auto fast_tag, auto full_tag) {
                     constexpr bool WHOLE = decltype(full_tag)::value;
                     const int nsteps = (rel_hi + 255) >> 8;
-                    for (int stp = 0; stp < nsteps; ++stp) {
-                        int p0, base;
-                        uint32_t hb, vm;
-                        step_head(full_tag, stp, p0, hb, base, vm);
-                        int ix[8];
-                        AT va[8];
-                        const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
-                        // products in register order, then back to position order
-                        AT rr[8][KB];
+                    int stp = 0;
+                    if constexpr (WHOLE && KB <= 2) {
+                        // two steps at a time: their fronts and scans are independent and interleave
+                        for (; stp + 1 < nsteps; stp += 2) {
+                            int p0a, p0b, basea, baseb;
+                            uint32_t hba, hbb;
+                            AT rra[8][KB], rrb[8][KB];
+                            seg_front(full_tag, stp, p0a, hba, basea, rra);
+                            seg_front(full_tag, stp + 1, p0b, hbb, baseb, rrb);
+                            const unsigned bala = __ballot_sync(FULL, hba != 0u);
+                            const unsigned balb = __ballot_sync(FULL, hbb != 0u);
+                            if ((bala | balb) == 0u) {
 #pragma unroll
-                        for (int b = 0; b < KB; ++b) {
-                            AT pr[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                AT w_ = AT(0);
-                                if (WHOLE || ((vm_r >> e) & 1u)) {
-                                    if constexpr (SMEMV) {
-                                        w_ = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e] * KB + b]);
-                                    } else {
-                                        w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + ix[e]));
-                                    }
-                                }
-                                pr[e] = va[e] * w_;
+                                for (int b = 0; b < KB; ++b) seg_carry_total(b, rra[7][b] + rrb[7][b]);
+                                continue;
                             }
-                            // lane-local inclusive prefix in position order, restarted at every head
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const AT pe = sw ? pr[e ^ 4] : pr[e];
-                                rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pe : rr[e > 0 ? e - 1 : 0][b] + pe;
-                            }
-                        }
-                        const unsigned bal = __ballot_sync(FULL, hb != 0u);
-                        if (bal == 0u) {
-                            // no segment starts in this step: add the step total to the open segment
 #pragma unroll
                             for (int b = 0; b < KB; ++b) {
-                                AT T = rr[7][b];
-#pragma unroll
-                                for (int d = 16; d >= 1; d >>= 1) T += __shfl_xor_sync(FULL, T, d);
-                                const AT s_ = chi[b] + T;  // compensated addition (TwoSum)
-                                const AT bp = s_ - chi[b];
-                                clo[b] += (chi[b] - (s_ - bp)) + (T - bp);
-                                chi[b] = s_;
+                                AT Texa, Texb;
+                                const AT Ta = seg_scan(bala, rra[7][b], Texa);
+                                const AT Tb = seg_scan(balb, rrb[7][b], Texb);
+                                const AT T31a = __shfl_sync(FULL, Ta, 31);
+                                const AT T31b = __shfl_sync(FULL, Tb, 31);
+                                seg_back(fast_tag, b, bala, p0a, hba, basea, rra, Texa, T31a);
+                                seg_back(fast_tag, b, balb, p0b, hbb, baseb, rrb, Texb, T31b);
                             }
+                        }
+                    }
+                    for (; stp < nsteps; ++stp) {
+                        int p0, base;
+                        uint32_t hb;
+                        AT rr[8][KB];
+                        seg_front(full_tag, stp, p0, hb, base, rr);
+                        const unsigned bal = __ballot_sync(FULL, hb != 0u);
+                        if (bal == 0u) {
+#pragma unroll
+                            for (int b = 0; b < KB; ++b) seg_carry_total(b, rr[7][b]);
                             continue;
                         }
-                        // warp segmented scan of the lanes' open sums (the o operator of Sec. IV-B)
-                        const unsigned le = bal & (FULL >> (31 - lane));
-                        const int seg_start = le ? (31 - __clz(le)) : 0;
-                        const bool before = (bal & ((1u << lane) - 1u)) != 0u;
-                        AT *ev = ev_base + p0;
 #pragma unroll
                         for (int b = 0; b < KB; ++b) {
-                            AT T = rr[7][b];
-#pragma unroll
-                            for (int d = 1; d < 32; d <<= 1) {
-                                const AT v = __shfl_up_sync(FULL, T, d);
-                                if (lane - d >= seg_start && lane >= d) T += v;
-                            }
-                            AT Tex = __shfl_up_sync(FULL, T, 1);
-                            if (lane == 0) Tex = AT(0);
-                            if (hb != 0u && b < kb) {
-                                // value closing at position e: the open sum up to e - 1 (0 at e = 0)
-                                if constexpr (sizeof(AT) == 4) {
-                                    const float4 lo = make_float4(0.f, rr[0][b], rr[1][b], rr[2][b]);
-                                    const float4 hi = make_float4(rr[3][b], rr[4][b], rr[5][b], rr[6][b]);
-                                    float4 *q = reinterpret_cast<float4 *>(ev);
-                                    q[sw] = sw ? hi : lo;  // staggered like the loads
-                                    q[sw ^ 1] = sw ? lo : hi;
-                                } else {
-#pragma unroll
-                                    for (int e = 1; e < 8; ++e) ev[e] = rr[e - 1][b];
-                                }
-                                // the first head closes the segment flowing into the lane
-                                const AT lead = Tex + (before ? AT(0) : chi[b] + clo[b]);
-                                uint32_t rem = hb;
-                                int k = 0;
-                                while (rem) {
-                                    const int e = __ffs(rem) - 1;
-                                    AT v = (e == 0) ? AT(0) : ev[e];
-                                    if (k == 0) v += lead;
-                                    emit(FAST ? i0 + base + k : col_search(p0 + e - 1), b, v);
-                                    rem &= rem - 1u;
-                                    ++k;
-                                }
-                            }
-                            chi[b] = __shfl_sync(FULL, T, 31);
-                            clo[b] = AT(0);
+                            AT Tex;
+                            const AT T = seg_scan(bal, rr[7][b], Tex);
+                            seg_back(fast_tag, b, bal, p0, hb, base, rr, Tex, __shfl_sync(FULL, T, 31));
                         }
                     }
                 };
@@ -612,16 +713,16 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                 } else if constexpr (MODE == MODE_SCATTER) {
                     if (win) {
                         if (dup)
-                            run_scatter8(BoolC<false>{}, BoolC<true>{}, BoolC<false>{});
+                            run_scatter(BoolC<false>{}, BoolC<true>{}, BoolC<false>{});
                         else if (full)
-                            run_scatter8(BoolC<true>{}, BoolC<true>{}, BoolC<true>{});
+                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{});
                         else
-                            run_scatter8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
                     } else {
                         if (dup)
-                            run_scatter8(BoolC<false>{}, BoolC<false>{}, BoolC<false>{});
+                            run_scatter(BoolC<false>{}, BoolC<false>{}, BoolC<false>{});
                         else
-                            run_scatter8(BoolC<true>{}, BoolC<false>{}, BoolC<false>{});
+                            run_scatter(BoolC<true>{}, BoolC<false>{}, BoolC<false>{});
                     }
                 } else {
                     if (!dup)
