@@ -120,6 +120,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The job's time: the longest timed region over the ranks (every rank calls this)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Aggregate GB/s of all replicas: every rank moves bytes_per_step per step."""
+    return bytes_per_step * steps * world / (ms_max / 1e3) / 1e9
+
+
 def pair_bytes(m, n, nnz, sv=4, sx=4, si=4, sp=4):
     """Algorithmic bytes (wide CSC): SpMV Z(si+sv)+(n+1)sp+n sx+m sx; SpVTM Z(si+sv)+(n+1)sp+m sx+n sx."""
     spmv_b = nnz * (si + sv) + (n + 1) * sp + n * sx + m * sx
@@ -206,6 +222,154 @@ def run_reference(args):
     return 0
 
 
+def time_pair_gbs(pkg, plan, m, n, nnz, layout, steps, sv=4, stream=None):
+    """GB/s of SpMV + SpVTM pairs on `plan` (device vectors, CUDA events), plus per-op kernel times."""
+    import torch
+
+    dev = plan.vals.device
+    g = torch.Generator(device=dev)
+    g.manual_seed(12)
+    x = torch.rand(n, generator=g, device=dev) * 2 - 1
+    v = torch.rand(m, generator=g, device=dev) * 2 - 1
+    y = torch.empty(m, device=dev)
+    u = torch.empty(n, device=dev)
+    stream = stream or torch.cuda.current_stream()
+    for _ in range(3):
+        pkg.spmv(plan.handle, x, y, stream)
+        pkg.spvtm(plan.handle, v, u, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        pkg.spmv(plan.handle, x, y, stream)
+        pkg.spvtm(plan.handle, v, u, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1) / steps
+    long_, short = (n, m) if layout == "csc" else (m, n)
+    b = 2 * (nnz * (4 + sv) + (long_ + 1) * 4 + (m + n) * 4)
+    return {"gbs": round(b / (ms / 1e3) / 1e9, 1), "ms_per_pair": round(ms, 4), "bytes_per_pair": b,
+            "frac_of_hbm_peak": round(b / (ms / 1e3) / 1e9 / load_peaks()[0], 4)}
+
+
+def batched_rate(pkg, plan, m, n, nnz, k, steps):
+    """Vectors/s and effective GB/s of k-vector SpMV and SpVTM passes (matrix streamed once per pass)."""
+    import torch
+
+    dev = plan.vals.device
+    g = torch.Generator(device=dev)
+    g.manual_seed(13)
+    X = torch.rand((k, n), generator=g, device=dev)
+    V = torch.rand((k, m), generator=g, device=dev)
+    out = {}
+    for op, inp, len_out in ((pkg.SPMV_OP_AX, X, m), (pkg.SPMV_OP_VTA, V, n)):
+        Y = torch.empty((k, len_out), device=dev)
+        for _ in range(2):
+            pkg.spmv_batch(plan.handle, op, k, inp, inp.stride(0), Y, Y.stride(0))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            pkg.spmv_batch(plan.handle, op, k, inp, inp.stride(0), Y, Y.stride(0))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        b = nnz * 8 + (n + 1) * 4 + k * (m + n) * 4
+        out["spmv" if op == pkg.SPMV_OP_AX else "spvtm"] = {
+            "ms": round(ms, 4), "vectors_per_s": round(k / (ms / 1e3), 1), "gbs": round(b / (ms / 1e3) / 1e9, 1)}
+    plan.check()
+    return out
+
+
+def serving_measurement(pkg, dev, seconds: float = 2.0, rates=(0.5, 0.8, 1.0)):
+    """Continuous batching over 64 resident matrices with Poisson-arriving requests of 1-32 vectors.
+
+    Capacity is measured first (a burst of requests, vectors completed per second); then requests
+    arrive at fractions of it for `seconds` each and every request's submit-to-result latency is
+    read back.  Returns vectors/s and p50/p99 latency per arrival rate.
+    """
+    import numpy as np
+    import torch
+
+    import synth
+
+    specs = synth.serving_specs()
+    t0 = time.time()
+    mats, plans = [], []
+    for sp in specs:
+        A = synth.serving_matrix(sp, device=dev)
+        plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout=A.layout)
+        mats.append(A)
+        plans.append(plan)
+    gen_s = time.time() - t0
+    g = torch.Generator(device=dev)
+    g.manual_seed(14)
+    bufs = []
+    for A in mats:
+        bufs.append({pkg.SPMV_OP_AX: (torch.rand((32, A.n), generator=g, device=dev), torch.empty((96, A.m), device=dev)),
+                     pkg.SPMV_OP_VTA: (torch.rand((32, A.m), generator=g, device=dev), torch.empty((96, A.n), device=dev))})
+    torch.cuda.synchronize()
+    srv = pkg.serve_create(int(120e9), 32, 4)
+    try:
+        ids = [pkg.serve_register(srv, p.handle) for p in plans]
+        rng = np.random.default_rng(4)
+        ring = [0] * len(mats)
+
+        def submit(i, op, k):
+            X, Y = bufs[i][op]
+            o = ring[i]
+            ring[i] = (o + k) % 64
+            return pkg.serve_submit(srv, ids[i], op, k, X, Y[o:o + k])
+
+        def draw():
+            return int(rng.integers(len(mats))), int(rng.integers(2)), int(rng.integers(1, 33))
+
+        # capacity: a burst of requests, all queued at once
+        burst = [draw() for _ in range(600)]
+        tb = time.perf_counter()
+        rids = [submit(*r) for r in burst]
+        for rid in rids:
+            pkg.serve_wait(srv, rid, 120_000)
+        cap_vps = sum(r[2] for r in burst) / (time.perf_counter() - tb)
+        mean_k = 16.5
+        res = {"matrices": len(mats), "nonzeros": int(sum(A.nnz for A in mats)), "generate_s": round(gen_s, 1),
+               "capacity_vectors_per_s": round(cap_vps, 1), "rates": []}
+        for frac in rates:
+            lam = frac * cap_vps / mean_k  # requests per second
+            st0 = pkg.serve_stats(srv)
+            rids, ks = [], []
+            t_start = time.perf_counter()
+            t_next = t_start
+            while True:
+                now = time.perf_counter()
+                if now - t_start >= seconds:
+                    break
+                if now < t_next:
+                    time.sleep(min(t_next - now, 0.0005))
+                    continue
+                i, op, k = draw()
+                rids.append(submit(i, op, k))
+                ks.append(k)
+                t_next += rng.exponential(1.0 / lam)
+            for rid in rids:
+                pkg.serve_wait(srv, rid, 120_000)
+            elapsed = time.perf_counter() - t_start
+            lat = np.array([pkg.serve_poll(srv, rid)[1] for rid in rids])
+            st1 = pkg.serve_stats(srv)
+            res["rates"].append({"offered_frac_of_capacity": frac, "requests": len(rids),
+                                 "vectors_per_s": round(sum(ks) / elapsed, 1),
+                                 "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                 "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                                 "launches": st1["launches"] - st0["launches"],
+                                 "max_inflight_launches": st1["max_inflight_launches"]})
+        return res
+    finally:
+        pkg.serve_destroy(srv)
+        for p in plans:
+            p.close()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -269,13 +433,9 @@ def run_ours(args):
     clocks = sampler.stop(t0, t1)
     plan.check()
     kt = {k: pkg.spmv_profile_read(plan.handle, k) for k in range(5)}
-    ms_t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     b_spmv, b_spvtm = pair_bytes(m, n, nnz)
-    total_bytes = (b_spmv + b_spvtm) * args.steps * world
-    value = total_bytes / (ms_max / 1e3) / 1e9
+    value = whole_job_gbs(b_spmv + b_spvtm, args.steps, world, ms_max)
 
     # roofline of the dominant kernel (chunk scatter = SpMV local, chunk dot = SpVTM local)
     peak, peak_src = load_peaks()
@@ -316,6 +476,16 @@ def run_ours(args):
                "ms_per_step": round(te * 1e3, 3), "api": "spmv/spvtm with pinned host vectors"}
 
     out = None
+    extras = None
+    if rank == 0 and world == 1 and not args.skip_extras:
+        extras = {}
+        extras["batched_k8"] = batched_rate(pkg, plan, m, n, nnz, 8, max(10, args.steps // 20))
+        vb = A.vals.to(torch.bfloat16)
+        pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32)
+        extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),
+                                     workload=WORKLOAD.replace("fp32", "bf16values"))
+        pb.close()
+        del vb
     if rank == 0:
         cpu = None
         if not args.skip_cpu_baseline and world == 1:
@@ -338,11 +508,24 @@ def run_ours(args):
                        "kernel_ms": {name: round(kt[k][0] / max(kt[k][1], 1), 4) for k, name in
                                      enumerate(["chunk_scatter", "combine", "chunk_segdot", "zone_fixup", "dvalues"])
                                      if kt[k][1]}},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "extras": extras,
                "gpu_launches": args.steps * (4 if info["zones"] > 0 else 3),
                "clocks": clocks}
-        print(json.dumps(out))
     plan.close()
+    if extras is not None:
+        del A, x, v, y, u
+        torch.cuda.empty_cache()
+        T = synth.tall_fp32_large(2, device=dev)
+        pt = pkg.Plan(T.m, T.n, T.ptr, T.idx, T.vals, layout="csr")
+        extras["tall_csr"] = dict(time_pair_gbs(pkg, pt, T.m, T.n, T.nnz, "csr", max(20, args.steps // 5)),
+                                  workload=f"tall_csr_m{T.m}_n{T.n}_fp32_powerlaw2.2_20dense", nnz=T.nnz)
+        pt.close()
+        del T, pt
+        torch.cuda.empty_cache()
+        if not args.skip_serving:
+            extras["serving"] = serving_measurement(pkg, dev)
+    if out is not None:
+        print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -359,6 +542,9 @@ def main(argv=None):
     ap.add_argument("--scale", type=float, default=1.0,
                     help="fraction of the 5M columns (a smaller sample of the same workload, for profiling)")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the tall CSR, BF16-value, batched and serving measurements")
+    ap.add_argument("--skip-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--warps", type=int, default=0, help="warps (chunks) per CTA; 0 = library default")
     ap.add_argument("--tile-items", type=int, default=0, help="merge items per staged tile; 0 = library default")
     ap.add_argument("--stages", type=int, default=0, help="staging buffers per warp; 0 = library default")

@@ -362,7 +362,7 @@ def tall_fp32_large(seed: int = 2, device="cuda", scale: float = 1.0, value_dtyp
 def serving_specs(seed: int = 4, count: int = 64, budget_bytes: float = 120e9):
     """Shapes of the resident serving matrices: list of dicts.
 
-    m in [1k, 50k], n in [100k, 5M], Z in [1M, 100M] (each log-uniform), Z
+    m in [1k, 50k], n in [100k, 5M] (multiples of 4), Z in [1M, 100M] (each log-uniform), Z
     capped at m*n/4; wide CSC or tall CSR with equal odds (a tall matrix
     swaps the roles: its long dimension is the row count).  The total stored
     bytes (8 per nonzero plus the pointer array) stay under ``budget_bytes``.
@@ -371,8 +371,10 @@ def serving_specs(seed: int = 4, count: int = 64, budget_bytes: float = 120e9):
     specs = []
     total = 0.0
     for i in range(count):
-        short = int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4)))))
-        long_ = int(round(math.exp(rng.uniform(math.log(1e5), math.log(5e6)))))
+        # dimensions rounded to multiples of 4, so that the vectors of a k-vector request
+        # packed back to back each start on a 16-byte boundary
+        short = 4 * int(round(math.exp(rng.uniform(math.log(1e3), math.log(5e4))) / 4))
+        long_ = 4 * int(round(math.exp(rng.uniform(math.log(1e5), math.log(5e6))) / 4))
         z = int(round(math.exp(rng.uniform(math.log(1e6), math.log(1e8)))))
         z = min(z, short * long_ // 4)
         layout = "csc" if rng.random() < 0.5 else "csr"
