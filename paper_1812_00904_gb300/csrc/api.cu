@@ -88,22 +88,57 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.masks = p->masks;
     sp.ntiles = p->ntiles;
     sp.mwp = p->mwp;
-    sp.stage_bytes = p->stage_bytes;
     sp.stages = p->S;
     sp.x_cap = p->x_cap;
+    sp.tile_cap = p->T;
     sp.rec_left = p->rec_left;
     sp.rec_right = p->rec_right;
     sp.err = p->err;
     return sp;
 }
 
-// Launch geometry of one streaming pass: W consumer warps + 1 producer warp per CTA.
-void set_geometry(const spmv_plan_s *p, LaunchArgs &a, size_t vec_elem, int kbt) {
+// Layout of one warp's staging slot: indices, values, segment-start masks and, for
+// the scatter and gradient modes, the long-vector windows (16-byte aligned).
+struct SlotGeom {
+    int off_val, off_mask, off_x, bytes;
+};
+SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
+    SlotGeom g;
+    g.off_val = (int)align_up((size_t)p->T * 4, 128);
+    g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
+    g.off_x = g.off_mask + (int)align_up((size_t)p->mwp * 4, 16);
+    const int nx = mode == MODE_SEGDOT ? 0 : mode == MODE_DVALUES ? 1 : kbt;
+    g.bytes = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 128);
+    return g;
+}
+// On-chip short-vector bytes of a pass (accumulator of the scatter mode, input otherwise).
+size_t vec_bytes(const spmv_plan_s *p, int mode, int kbt) {
+    if (!p->onchip) return 0;
+    const size_t e = mode == MODE_SCATTER ? (size_t)p->sa : (size_t)p->sx;
+    return align_up((size_t)p->n_minor * kbt * e, 128);
+}
+// Warps per CTA of a pass: the plan's warps, as many as the shared memory holds.
+int warps_for(const spmv_plan_s *p, int mode, int kbt) {
+    const size_t vec = vec_bytes(p, mode, kbt);
+    const SlotGeom g = slot_geom(p, mode, kbt);
+    const size_t room = (size_t)p->smem_max > vec + BAR_BYTES ? (size_t)p->smem_max - vec - BAR_BYTES : 0;
+    const int fit = (int)std::min<size_t>(room / ((size_t)p->S * g.bytes), 64);
+    return std::min({p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
+}
+
+// Launch geometry of one streaming pass.
+void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt) {
+    const SlotGeom g = slot_geom(p, mode, kbt);
+    const int W = std::max(1, warps_for(p, mode, kbt));
     a.smemv = p->onchip;
-    a.sp.vec_region_bytes = p->onchip ? (int)align_up((size_t)p->n_minor * kbt * vec_elem, 128) : 0;
-    a.smem = a.sp.vec_region_bytes + p->smem_base;
+    a.sp.vec_region_bytes = (int)vec_bytes(p, mode, kbt);
+    a.sp.stage_bytes = g.bytes;
+    a.sp.off_val = g.off_val;
+    a.sp.off_mask = g.off_mask;
+    a.sp.off_x = g.off_x;
+    a.smem = a.sp.vec_region_bytes + BAR_BYTES + W * p->S * g.bytes;
     a.grid = p->ctas;
-    a.block = (std::min(p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS) + 1) * 32;
+    a.block = W * 32;
 }
 
 enum PtrKind { PK_DEVICE, PK_HOST, PK_BAD };
@@ -151,7 +186,7 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     a.sp = base_params(p);
     a.sp.kb = kb;
     for (int b = 0; b < kb; ++b) a.sp.vin[b] = in[b];
-    set_geometry(p, a, p->sa, kb_template(kb));
+    set_geometry(p, a, MODE_SCATTER, kb_template(kb));
     a.sp.part = p->part;
     if (!p->onchip) CUDA_TRY(cudaMemsetAsync(p->part, 0, (size_t)p->n_minor * sizeof(double), s));
     a.stream = s;
@@ -188,7 +223,7 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
         a.sp.vin[b] = in[b];
         a.sp.vout[b] = out[b];
     }
-    set_geometry(p, a, p->sx, kb_template(kb));
+    set_geometry(p, a, MODE_SEGDOT, kb_template(kb));
     a.stream = s;
     {
         ProfScope ps(p, 2, s);
@@ -211,7 +246,7 @@ static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, voi
     a.sp.vin[0] = csc ? r : x;
     a.sp.vin[1] = csc ? x : r;
     a.sp.vout[0] = g;
-    set_geometry(p, a, p->sx, 1);
+    set_geometry(p, a, MODE_DVALUES, 1);
     a.stream = s;
     ProfScope ps(p, 4, s);
     CUDA_TRY(launch_stream(p, MODE_DVALUES, 1, a));
@@ -349,40 +384,32 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     // ---- launch configuration: tiles of T nonzeros, rounds of W tiles, S stages per CTA
     p->T = (opts && opts->tile_items) ? opts->tile_items : 512;
     p->S = (opts && opts->stages) ? opts->stages : 2;
-    int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : 16;
+    int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : MAX_WARPS;
     if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
     if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 24]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
-    const int elem = std::max(p->sa, p->sx);
-    auto stage_for = [&](int w, int bw) {
-        const size_t xcap = align_up((size_t)w * p->T / 4 + 64, 8);
-        return align_up(64 + align_up((size_t)(w + 1) * 16, 16) + ((size_t)w * p->T + 16) * (4 + p->sv) +
-                            (size_t)w * p->mwp * 4 + (size_t)bw * xcap * p->sx,
-                        128);
-    };
-    const size_t vec1 = align_up((size_t)p->n_minor * elem, 128);
-    p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL) &&
-                vec1 + 128 + (size_t)p->S * stage_for(std::min(W, 4), 1) <= (size_t)smem_max;
-    const size_t vec_used = p->onchip ? vec1 : 0;
-    while (W > 1 && vec_used + 128 + (size_t)p->S * stage_for(W, 1) > (size_t)smem_max) --W;
-    if (vec_used + 128 + (size_t)p->S * stage_for(W, 1) > (size_t)smem_max)
-        return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
+    p->x_cap = (int)align_up((size_t)p->T / 4 + 16, 8);  // columns of a tile's window (fall back to global beyond)
+    p->smem_max = smem_max;
     p->W = W;
+    // the short vector on chip when it leaves room for at least 4 warps of the scatter pass
+    p->onchip = !(flags & SPMV_PLAN_SHORT_IN_GLOBAL);
+    if (p->onchip && warps_for(p, MODE_SCATTER, 1) < std::min(W, 4)) p->onchip = false;
+    for (int mode : {MODE_SCATTER, MODE_SEGDOT, MODE_DVALUES})
+        if (warps_for(p, mode, 1) < 1) return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
+    // vectors per pass of spmv_batch: as many as still leave most of the warps
     p->batch_width = 1;
     if (p->onchip) {
+        const int want = std::min(warps_for(p, MODE_SCATTER, 1), 12);
         for (int kb : {8, 4, 2}) {
-            if (align_up((size_t)p->n_minor * kb * elem, 128) + 128 + (size_t)p->S * stage_for(W, kb) <=
-                (size_t)smem_max) {
+            if (warps_for(p, MODE_SCATTER, kb) >= want && warps_for(p, MODE_SEGDOT, kb) >= want) {
                 p->batch_width = kb;
                 break;
             }
         }
     }
-    p->x_cap = (int)align_up((size_t)W * p->T / 4 + 64, 8);
-    p->stage_bytes = (int)stage_for(W, p->batch_width);
-    p->smem_base = 128 + p->S * p->stage_bytes;
+    p->W_info = warps_for(p, MODE_SCATTER, 1);
     // reporting chunks: the paper's P (default: one per warp of a full GPU wave); execution
     // tiles: T consecutive nonzeros each, every tile a processor of the kernels
     const int64_t nt64 = (nnz + p->T - 1) / p->T;
@@ -524,7 +551,7 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->vec_dtype = p->vec_t;
     info->chunks = p->P;
     info->ctas = p->ctas;
-    info->warps_per_cta = p->W;
+    info->warps_per_cta = p->W_info;
     info->tile_items = p->T;
     info->stages = p->S;
     info->tiles = p->ntiles;

@@ -15,9 +15,10 @@ enum Mode : int {
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
-constexpr int MAX_WARPS = 24;    // consumer warps per CTA (plus one producer warp), one vector per pass
-constexpr int MAX_WARPS_KB = 16; // consumer warps per CTA of the multi-vector passes (more registers per thread)
-constexpr int MAX_STAGES = 4;
+constexpr int MAX_WARPS = 24;    // warps per CTA of the single-vector passes
+constexpr int MAX_WARPS_KB = 16; // warps per CTA of the multi-vector passes (more registers per thread)
+constexpr int MAX_STAGES = 4;    // slots per warp
+constexpr int BAR_BYTES = 1024;  // slot barriers at the start of the staging area
 
 // Per-chunk descriptor produced by the set-up (32 bytes).
 struct ChunkDev {
@@ -56,7 +57,8 @@ struct StreamParams {
     const TileMeta *meta;    // ntiles + 1 entries
     const uint32_t *masks;   // per tile: mwp words of segment-start bits
     int32_t ntiles, mwp;
-    int32_t stage_bytes, vec_region_bytes, stages, x_cap;  // x_cap: window elements per vector
+    int32_t stage_bytes, vec_region_bytes, stages, x_cap;  // per-warp slot bytes, slots per warp, window elements
+    int32_t tile_cap, off_val, off_mask, off_x;           // slot layout: indices at 0, values, masks, windows
     int32_t kb;              // vectors in this pass (<= KB template)
     const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
     void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g

@@ -23,8 +23,9 @@ struct spmv_plan_s {
     // launch configuration
     int P = 0;          // reporting chunks (the paper's P; spmv_plan_chunks)
     int ntiles = 0;     // execution tiles (every tile a processor of the kernels)
-    int ctas = 0, W = 0, T = 0, S = 0;
-    int stage_bytes = 0, mwp = 0, x_cap = 0, pptr_len = 0, smem_base = 0;
+    int ctas = 0, W = 0, T = 0, S = 0;  // W: most warps per CTA (each pass fits what shared memory holds)
+    int W_info = 0;                       // warps of the single-vector scatter pass (spmv_plan_info)
+    int mwp = 0, x_cap = 0, pptr_len = 0, smem_max = 0;  // masks words per tile, window elements per tile
     bool onchip = false;
     int batch_width = 1;
 

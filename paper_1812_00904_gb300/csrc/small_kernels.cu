@@ -1,7 +1,7 @@
 // Cross-chunk combines: the sum of the per-CTA partial short vectors (the
 // Allreduce of Sec. III) and the overlap-zone fixup (the per-zone reductions of
-// Sec. IV-A).  Both add in FP64 in a fixed order, so results do not depend on
-// which CTA finished first.
+// Sec. IV-A).  Both add in a fixed order, so results do not depend on which CTA
+// finished first: FP32 data in compensated FP32 pairs, FP64 data in FP64.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -13,32 +13,8 @@ struct OutPtrs {
     void *p[KB_MAX];
 };
 
-// out_b[i] = sum_{q < nparts} part[(q * kb + b) * n_minor + i]
-template <typename XT, typename PT>
-__global__ void __launch_bounds__(256) combine_kernel(const PT *__restrict__ part, int nparts, int n_minor, int kb,
-                                                      OutPtrs out) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int b = blockIdx.y;
-    if (i >= n_minor) return;
-    const PT *src = part + (size_t)b * n_minor + i;
-    const size_t stride = (size_t)kb * n_minor;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int q = 0;
-    // four independent loads in flight; the final order (s0+s1)+(s2+s3) is fixed
-    for (; q + 4 <= nparts; q += 4) {
-        s0 += static_cast<double>(__ldg(src + (size_t)(q + 0) * stride));
-        s1 += static_cast<double>(__ldg(src + (size_t)(q + 1) * stride));
-        s2 += static_cast<double>(__ldg(src + (size_t)(q + 2) * stride));
-        s3 += static_cast<double>(__ldg(src + (size_t)(q + 3) * stride));
-    }
-    for (; q < nparts; ++q) s0 += static_cast<double>(__ldg(src + (size_t)q * stride));
-    static_cast<XT *>(out.p[b])[i] = static_cast<XT>((s0 + s1) + (s2 + s3));
-}
-
-// Zone k spans tiles S_k = [first, last]: u_{j_k} = right record of the first
-// tile + whole-tile records of the middle tiles + left record of the last.
-// Records are (hi, lo) pairs of the accumulation type, added with
-// compensated (TwoSum) arithmetic in that type in a fixed order.
+// Compensated addition (TwoSum): s + c accumulates v with the rounding error of
+// every addition kept in c.  The error term is exact whatever the operand order.
 template <typename T> __device__ __forceinline__ void two_sum_add(T &s, T &c, T v) {
     const T t = s + v;
     const T bp = t - s;
@@ -46,6 +22,46 @@ template <typename T> __device__ __forceinline__ void two_sum_add(T &s, T &c, T 
     s = t;
 }
 
+// out_b[i] = sum_{q < nparts} part[(q * kb + b) * n_minor + i].  A block takes 32
+// consecutive elements; its 8 thread rows sum the partials q = row, row + 8, ... and
+// the 8 row sums are added in row order: a fixed order, independent of timing.
+// FP32 partials are added with TwoSum in FP32 pairs (about twice the FP32 precision,
+// without the FP64 pipe); FP64 partials in FP64.
+constexpr int COMB_X = 32, COMB_Y = 8;
+template <typename XT, typename PT>
+__global__ void __launch_bounds__(COMB_X * COMB_Y) combine_kernel(const PT *__restrict__ part, int nparts, int n_minor,
+                                                                  int kb, OutPtrs out) {
+    using T = PT;
+    __shared__ T sh_s[COMB_Y][COMB_X], sh_c[COMB_Y][COMB_X];
+    const int i = blockIdx.x * COMB_X + threadIdx.x;
+    const int b = blockIdx.y;
+    const int row = threadIdx.y;
+    T s = T(0), c = T(0);
+    if (i < n_minor) {
+        const PT *src = part + (size_t)b * n_minor + i;
+        const size_t stride = (size_t)kb * n_minor;
+#pragma unroll 4
+        for (int q = row; q < nparts; q += COMB_Y) two_sum_add(s, c, __ldg(src + (size_t)q * stride));
+    }
+    sh_s[row][threadIdx.x] = s;
+    sh_c[row][threadIdx.x] = c;
+    __syncthreads();
+    if (row == 0 && i < n_minor) {
+        T ts = sh_s[0][threadIdx.x], tc = sh_c[0][threadIdx.x];
+#pragma unroll
+        for (int r = 1; r < COMB_Y; ++r) {
+            two_sum_add(ts, tc, sh_s[r][threadIdx.x]);
+            tc += sh_c[r][threadIdx.x];
+        }
+        static_cast<XT *>(out.p[b])[i] = static_cast<XT>(ts + tc);
+    }
+}
+
+// Zone k spans tiles S_k = [first, last]: u_{j_k} = right record of the first
+// tile + the records of the middle tiles (whole-tile sums, kept as right records)
+// + left record of the last, added in this order with TwoSum in the accumulation
+// type.  One thread per zone (most zones span two tiles); the loads of a long zone
+// are issued four at a time.  Every zone's column is written once.
 template <typename XT, typename T, typename RT>
 __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ zones, int z,
                                                     const RT *__restrict__ rec_left, const RT *__restrict__ rec_right,
@@ -56,13 +72,24 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
     for (int b = 0; b < kb; ++b) {
         const RT *rr = rec_right + (size_t)b * P;
         const RT f = rr[zd.first];
+        const RT l = rec_left[(size_t)b * P + zd.last];
         T s = f.x, c = f.y;
-        for (int q = zd.first + 1; q < zd.last; ++q) {
+        int q = zd.first + 1;
+        for (; q + 4 <= zd.last; q += 4) {
+            RT m[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) m[e] = rr[q + e];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                two_sum_add(s, c, m[e].x);
+                c += m[e].y;
+            }
+        }
+        for (; q < zd.last; ++q) {
             const RT m = rr[q];
             two_sum_add(s, c, m.x);
             c += m.y;
         }
-        const RT l = rec_left[(size_t)b * P + zd.last];
         two_sum_add(s, c, l.x);
         c += l.y;
         static_cast<XT *>(out.p[b])[zd.col] = static_cast<XT>(s + c);
@@ -74,13 +101,13 @@ cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int np
     if (n_minor <= 0) return cudaSuccess;
     OutPtrs o;
     for (int b = 0; b < KB_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
-    dim3 grid((n_minor + 255) / 256, kb);
+    const dim3 grid((n_minor + COMB_X - 1) / COMB_X, kb), block(COMB_X, COMB_Y);
     if (vec_f64) {
-        combine_kernel<double, double><<<grid, 256, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
+        combine_kernel<double, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
     } else if (part_f64) {
-        combine_kernel<float, double><<<grid, 256, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
+        combine_kernel<float, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
     } else {
-        combine_kernel<float, float><<<grid, 256, 0, s>>>(static_cast<const float *>(part), nparts, n_minor, kb, o);
+        combine_kernel<float, float><<<grid, block, 0, s>>>(static_cast<const float *>(part), nparts, n_minor, kb, o);
     }
     return cudaGetLastError();
 }

@@ -1,8 +1,11 @@
 // Streaming kernel: the nonzeros are cut into equal-count tiles (the Sec. II
-// partition, every tile a "processor"); each CTA streams a contiguous range of
-// tiles through shared memory in rounds of W consecutive tiles.  A producer
-// warp stages a whole round with one bulk (TMA) copy per array; each of the W
-// consumer warps then processes one tile of the round.
+// partition, every tile a "processor"); each CTA takes a contiguous range of
+// tiles by the same rule, and within a CTA warp w takes tiles w, w + W, w + 2W, ...
+// Every warp streams its own tiles through S shared-memory slots of its own:
+// when it has finished a tile it issues the bulk (TMA) copies of the tile S
+// ahead into the freed slot (one copy per array: indices, values, segment-start
+// masks and, for the scatter and gradient modes, the window of the long vector
+// the tile needs), so no warp ever waits for another.
 //
 // Terms.  "major" is the compressed dimension (columns of a wide CSC matrix,
 // rows of a tall CSR matrix), "minor" the indexed one.  Segment j ends after
@@ -27,17 +30,7 @@
 namespace gbk {
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per pipeline wait
-constexpr int STAGE_HDR_BYTES = 64;                  // round geometry at the start of every stage
-
-struct alignas(16) RoundHdr {  // 64 bytes, written by the producer into the stage header
-    int t0, ntl;          // tiles [t0, t0 + ntl)
-    int kb0, ncov;        // staged nonzero cover [kb0, kb0 + ncov), kb0 a multiple of 8
-    int xbase, nxc;       // staged major-vector cover [xbase, xbase + nxc) (per vector)
-    int off_meta, off_idx, off_val, off_mask, off_x;  // byte offsets after the header
-    int win;              // 1: major-vector windows staged (else read from global memory)
-    int ok;               // 1: the round fits the stage (else refused, error word set)
-    int pad[3];
-};
+constexpr int BAR_REGION_BYTES = 1024;               // the warps' slot barriers (at most 32 warps x 4 slots)
 
 __device__ __forceinline__ void copy_elem(unsigned char *d, const unsigned char *s, int es) {
     if (es == 8) {
@@ -47,10 +40,6 @@ __device__ __forceinline__ void copy_elem(unsigned char *d, const unsigned char 
     } else {
         *reinterpret_cast<unsigned short *>(d) = *reinterpret_cast<const unsigned short *>(s);
     }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 template <typename XT> __device__ __forceinline__ XT zero_of() { return XT(0); }
@@ -67,27 +56,26 @@ template <bool B> struct BoolC {
 };
 
 template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
-__global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
+__global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
     using AT = typename Acc<VT>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int W = (blockDim.x >> 5) - 1;  // consumer warps; warp W is the producer
+    const int W = blockDim.x >> 5;
     const int kb = (MODE == MODE_DVALUES) ? 1 : p.kb;
     const int nvec = (MODE == MODE_DVALUES) ? 1 : p.kb;
     const int S = p.stages;
     const unsigned n_minor = static_cast<unsigned>(p.n_minor);
 
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes);
-    uint64_t *empty = full + MAX_STAGES;
-    unsigned char *stages = smem + p.vec_region_bytes + 128;
+    uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
+    unsigned char *myslots = smem + p.vec_region_bytes + BAR_REGION_BYTES + (size_t)warp * S * p.stage_bytes;
 
-    // this CTA's tiles: the Sec. II rule over the grid
+    // this CTA's tiles: the Sec. II rule over the grid; this warp's: ta + warp + k W
     const int G = gridDim.x, g = blockIdx.x;
     const int tq = p.ntiles / G, tr = p.ntiles % G;
     const int ta = g * tq + min(g, tr);
     const int tb = ta + tq + (g < tr ? 1 : 0);
-    const int nrounds = (tb - ta + W - 1) / W;
+    const int nk = (tb - ta > warp) ? (tb - ta - warp + W - 1) / W : 0;
 
     // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES)
     if constexpr (SMEMV) {
@@ -103,176 +91,152 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
             }
         }
     }
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < S; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], W);
-        }
+    if (lane == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&myfull[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (warp == W) {
-        // ================= producer warp =================
-        // tile descriptors, a block of 32 per register (one per lane), the next block prefetched
-        int bcur = 0;
-        int2 dcur = make_int2(0, 0), dnext = make_int2(0, 0);
-        auto load_block = [&](int blk) -> int2 {
-            const int t = ta + blk * 32 + lane;
-            const TileMeta m = p.meta[min(t, p.ntiles)];
-            return make_int2(m.nzb, m.e_begin);
-        };
-        auto meta_at = [&](int t) -> int2 {  // t in [ta, tb]; its block is bcur or bcur + 1
-            const int blk = (t - ta) >> 5;
-            const int2 src = (blk == bcur) ? dcur : dnext;
-            int2 r;
-            r.x = __shfl_sync(FULL, src.x, (t - ta) & 31);
-            r.y = __shfl_sync(FULL, src.y, (t - ta) & 31);
-            return r;
-        };
-        dcur = load_block(0);
-        dnext = load_block(1);
-        int s = 0;
-        uint32_t ph = 0;
-        for (int r = 0; r < nrounds; ++r) {
-            if (r >= S) {  // wait until every consumer released this stage
-                bool ok = mbar_wait_bounded(&empty[s], ph ^ 1u, WAIT_LIMIT_NS);
-                ok = __all_sync(FULL, ok);
-                if (!ok) {
-                    if (lane == 0) atomicOr(p.err, ERR_WAIT);
-                    break;
-                }
-            }
-            const int t0 = ta + r * W;
-            const int ntl = min(W, tb - t0);
-            const int t1 = t0 + ntl;
-            while (((t1 - ta) >> 5) > bcur + 1 || ((t0 - ta) >> 5) > bcur) {
-                dcur = dnext;
-                ++bcur;
-                dnext = load_block(bcur + 1);
-            }
-            const int2 m0 = meta_at(t0), m1 = meta_at(t1);
-            RoundHdr h;
-            h.t0 = t0;
-            h.ntl = ntl;
-            h.kb0 = m0.x & ~7;
-            h.ncov = ((m1.x + 7) & ~7) - h.kb0;
-            h.off_meta = 0;
-            h.off_idx = ((ntl + 1) * 16 + 15) & ~15;
-            h.off_val = h.off_idx + h.ncov * 4;
-            h.off_mask = h.off_val + h.ncov * (int)sizeof(VT);
-            h.off_x = h.off_mask + ntl * p.mwp * 4;
-            h.xbase = 0;
-            h.nxc = 0;
-            if (MODE != MODE_SEGDOT) {
-                constexpr int xa = 16 / (int)sizeof(XT);
-                const int last = min(m1.y, p.n_major - 1);
-                if (last >= m0.y) {
-                    h.xbase = m0.y & ~(xa - 1);
-                    h.nxc = ((last + 1 + xa - 1) & ~(xa - 1)) - h.xbase;
-                }
-            }
-            const int cap = p.stage_bytes - STAGE_HDR_BYTES;
-            h.win = (h.nxc <= p.x_cap) ? 1 : 0;
-            h.ok = (h.off_x <= cap && h.ncov >= 0) ? 1 : 0;
-            h.pad[0] = h.pad[1] = h.pad[2] = 0;
-            unsigned char *st = stages + s * p.stage_bytes;
-            unsigned char *d = st + STAGE_HDR_BYTES;
-            // one staged array per lane, in one instruction stream: 0 tile descriptors,
-            // 1 indices, 2 values, 3 segment-start masks, 4.. major-vector windows
-            const void *src = p.meta;
-            unsigned char *dst = d;
-            int e0 = t0, cnt = ntl + 1, len = p.ntiles + 1, es = 16;
-            if (lane == 1) {
-                src = p.idx;
-                dst = d + h.off_idx;
-                e0 = h.kb0;
-                cnt = h.ncov;
-                len = p.nnz;
-                es = 4;
-            } else if (lane == 2) {
-                src = p.vals;
-                dst = d + h.off_val;
-                e0 = h.kb0;
-                cnt = h.ncov;
-                len = p.nnz;
-                es = (int)sizeof(VT);
-            } else if (lane == 3) {
-                src = p.masks;
-                dst = d + h.off_mask;
-                e0 = t0 * p.mwp;
-                cnt = ntl * p.mwp;
-                len = p.ntiles * p.mwp;
-                es = 4;
-            } else if (lane >= 4) {
-                const int b = lane - 4;
-                src = (MODE == MODE_DVALUES) ? p.vin[1] : p.vin[b < KB_MAX ? b : 0];
-                dst = d + h.off_x + b * p.x_cap * (int)sizeof(XT);
-                e0 = h.xbase;
-                cnt = (MODE != MODE_SEGDOT && h.win && b < nvec) ? h.nxc : 0;
-                len = p.n_major;
-                es = (int)sizeof(XT);
-            }
-            if (!h.ok) cnt = 0;
-            // the part below the array's last 16-byte boundary by bulk copy, the rest
-            // (at most 15 bytes at the very end of an array) by plain loads
-            const int al = 16 / es;
-            const int lim = len & ~(al - 1);
-            const int end = e0 + cnt;
-            const int bend = min(end, lim);
-            const uint32_t bytes = bend > e0 ? static_cast<uint32_t>(bend - e0) * es : 0u;
-            if (cnt > 0 && end > lim) {
-                const int tl = min(end, len);
-                for (int e = max(e0, lim); e < tl; ++e)
-                    copy_elem(dst + (size_t)(e - e0) * es, static_cast<const unsigned char *>(src) + (size_t)e * es,
-                              es);
-            }
-            if (lane == 0) *reinterpret_cast<RoundHdr *>(st) = h;
-            const uint32_t total = __reduce_add_sync(FULL, bytes);
-            __syncwarp();
-            // releases the header and the plain stores; the bulk bytes complete the phase
-            if (lane == 0) mbar_arrive_expect_tx(&full[s], total);
-            if (bytes) bulk_g2s(dst, static_cast<const unsigned char *>(src) + (size_t)e0 * es, bytes, &full[s]);
-            if (++s == S) {
-                s = 0;
-                ph ^= 1u;
+    // ---- tile descriptors of this warp, 32 per batch: lane j holds tile 32 * batch + j
+    int4 dcur = make_int4(0, 0, 0, 0), dnxt = make_int4(0, 0, 0, 0);  // nzb, e_begin, flags, next tile's nzb
+    int ecur = 0, enxt = 0;                                            // next tile's e_begin
+    auto load_batch = [&](int bi, int4 &d, int &e1) {
+        const int k = (bi << 5) + lane;
+        if (k < nk) {
+            const int t = ta + warp + k * W;
+            const TileMeta a = p.meta[t];
+            const TileMeta b = p.meta[t + 1];
+            d = make_int4(a.nzb, a.e_begin, a.flags, b.nzb);
+            e1 = b.e_begin;
+        }
+    };
+    int cb = 0;  // batch held in dcur
+    load_batch(0, dcur, ecur);
+    load_batch(1, dnxt, enxt);
+    // descriptor of this warp's tile k (its batch is cb or cb + 1)
+    auto desc = [&](int k, int4 &d, int &e1) {
+        const bool c = (k >> 5) == cb;
+        const int src = k & 31;
+        d.x = __shfl_sync(FULL, c ? dcur.x : dnxt.x, src);
+        d.y = __shfl_sync(FULL, c ? dcur.y : dnxt.y, src);
+        d.z = __shfl_sync(FULL, c ? dcur.z : dnxt.z, src);
+        d.w = __shfl_sync(FULL, c ? dcur.w : dnxt.w, src);
+        e1 = __shfl_sync(FULL, c ? ecur : enxt, src);
+    };
+    // window [xbase, xbase + nxc) of the long vector covering segments i0..i1 (16-byte aligned)
+    auto xwindow = [&](int i0, int i1, int &xbase, int &nxc) {
+        xbase = 0;
+        nxc = 0;
+        if constexpr (MODE != MODE_SEGDOT) {
+            constexpr int xa = 16 / (int)sizeof(XT);
+            const int last = min(i1, p.n_major - 1);
+            if (last >= i0) {
+                xbase = i0 & ~(xa - 1);
+                nxc = ((last + 1 + xa - 1) & ~(xa - 1)) - xbase;
             }
         }
-    } else {
-        // ================= consumer warps: tile t0 + warp of every round =================
-        int s = 0;
-        uint32_t ph = 0;
-        for (int r = 0; r < nrounds; ++r) {
-            unsigned char *st = stages + s * p.stage_bytes;
-            bool ok = mbar_wait_bounded(&full[s], ph, WAIT_LIMIT_NS);
-            ok = __all_sync(FULL, ok);
-            if (!ok) {
-                if (lane == 0) atomicOr(p.err, ERR_WAIT);
-                break;
+    };
+    // Every lane copies one array for the whole kernel: lane 0 indices, 1 values,
+    // 2 segment-start masks, 3.. long-vector windows (one per vector).  Its source,
+    // element size and destination offset within a slot are fixed.
+    const unsigned char *c_src = reinterpret_cast<const unsigned char *>(p.idx);
+    int c_off = 0, c_len = p.nnz, c_es = 4;
+    bool c_x = false;  // a long-vector window lane in use
+    if (lane == 1) {
+        c_src = static_cast<const unsigned char *>(p.vals);
+        c_off = p.off_val;
+        c_es = (int)sizeof(VT);
+    } else if (lane == 2) {
+        c_src = reinterpret_cast<const unsigned char *>(p.masks);
+        c_off = p.off_mask;
+        c_len = p.ntiles * p.mwp;
+    } else if (lane >= 3) {
+        const int b = lane - 3;
+        c_src = static_cast<const unsigned char *>((MODE == MODE_DVALUES) ? p.vin[1] : p.vin[b < KB_MAX ? b : 0]);
+        c_off = p.off_x + b * p.x_cap * (int)sizeof(XT);
+        c_len = p.n_major;
+        c_es = (int)sizeof(XT);
+        c_x = MODE != MODE_SEGDOT && b < nvec;
+    }
+    const int c_lim = c_len & ~(16 / c_es - 1);  // the array's last 16-byte boundary (in elements)
+    // issue the copies of tile k into slot s
+    auto issue = [&](int k, int s) {
+        int4 d;
+        int e1;
+        desc(k, d, e1);
+        const int kb0 = d.x & ~7;
+        const int ncov = ((d.w + 7) & ~7) - kb0;
+        int xbase, nxc;
+        xwindow(d.y, e1, xbase, nxc);
+        int e0 = kb0, cnt = ncov;
+        if (lane == 2) {
+            e0 = (ta + warp + k * W) * p.mwp;
+            cnt = p.mwp;
+        } else if (lane >= 3) {
+            e0 = xbase;
+            cnt = (c_x && nxc <= p.x_cap) ? nxc : 0;
+        }
+        if (ncov < 0 || ncov > p.tile_cap) cnt = 0;
+        unsigned char *dst = myslots + (size_t)s * p.stage_bytes + c_off;
+        // the part below the array's last 16-byte boundary by bulk copy, the rest
+        // (at most 15 bytes at the very end of an array) by plain loads
+        const int end = e0 + cnt;
+        const int bend = min(end, c_lim);
+        const uint32_t bytes = bend > e0 ? static_cast<uint32_t>(bend - e0) * c_es : 0u;
+        if (cnt > 0 && end > c_lim) {
+            const int tl = min(end, c_len);
+            for (int e = max(e0, c_lim); e < tl; ++e)
+                copy_elem(dst + (size_t)(e - e0) * c_es, c_src + (size_t)e * c_es, c_es);
+        }
+        const uint32_t total = __reduce_add_sync(FULL, bytes);
+        __syncwarp();
+        // releases the plain stores; the bulk bytes complete the phase
+        if (lane == 0) mbar_arrive_expect_tx(&myfull[s], total);
+        if (bytes) bulk_g2s(dst, c_src + (size_t)e0 * c_es, bytes, &myfull[s]);
+    };
+
+    for (int k = 0; k < min(S, nk); ++k) issue(k, k);
+
+    int s = 0;        // slot of tile k
+    uint32_t ph = 0;  // phase parity of that slot's barrier
+    for (int k = 0; k < nk; ++k) {
+        unsigned char *slot = myslots + (size_t)s * p.stage_bytes;
+        bool ok = mbar_wait_bounded(&myfull[s], ph, WAIT_LIMIT_NS);
+        ok = __all_sync(FULL, ok);
+        if (!ok) {
+            if (lane == 0) atomicOr(p.err, ERR_WAIT);
+            // let the copies still in flight into this warp's slots land before leaving
+            for (int q = 0; q < min(S, nk - k); ++q) {
+                const int qs = s + q < S ? s + q : s + q - S;
+                mbar_wait_bounded(&myfull[qs], s + q < S ? ph : ph ^ 1u, WAIT_LIMIT_NS);
             }
-            const RoundHdr h = *reinterpret_cast<const RoundHdr *>(st);
-            const unsigned char *dat = st + STAGE_HDR_BYTES;
-            if (!h.ok) {
-                if (lane == 0) atomicOr(p.err, ERR_STRUCT);
-            } else if (warp < h.ntl) {
-                const int t = h.t0 + warp;
-                const TileMeta me = reinterpret_cast<const TileMeta *>(dat + h.off_meta)[warp];
-                const TileMeta nx = reinterpret_cast<const TileMeta *>(dat + h.off_meta)[warp + 1];
-                const int i0 = me.e_begin, i1 = nx.e_begin;
-                const bool needLeft = (me.flags & 1) != 0;
-                const bool needRight = (me.flags & 2) != 0;
-                const bool dup = (me.flags & 4) != 0;
-                const bool win = h.win != 0;
-                const int kb0 = me.nzb & ~7;
-                const int off = kb0 - h.kb0;  // a multiple of 8 elements
-                const int rel_lo = me.nzb - kb0;
-                const int rel_hi = nx.nzb - kb0;
+            break;
+        }
+        int4 d;
+        int e1;
+        desc(k, d, e1);
+        const int kb0 = d.x & ~7;
+        const int ncov = ((d.w + 7) & ~7) - kb0;
+        if (ncov < 0 || ncov > p.tile_cap) {
+            if (lane == 0) atomicOr(p.err, ERR_STRUCT);
+        } else {
+            {
+                const int t = ta + warp + k * W;
+                const int i0 = d.y, i1 = e1;
+                const bool needLeft = (d.z & 1) != 0;
+                const bool needRight = (d.z & 2) != 0;
+                const bool dup = (d.z & 4) != 0;
+                int xbase, nxc;
+                xwindow(i0, i1, xbase, nxc);
+                const bool win = nxc <= p.x_cap;
+                const int rel_lo = d.x - kb0;
+                const int rel_hi = d.w - kb0;
                 const bool full = rel_lo == 0 && (rel_hi & 255) == 0;  // whole 256-position steps only
-                const int32_t *idx_s = reinterpret_cast<const int32_t *>(dat + h.off_idx) + off;
-                const unsigned char *val_s = dat + h.off_val + (size_t)off * sizeof(VT);
-                const XT *x_s = reinterpret_cast<const XT *>(dat + h.off_x);
-                const uint32_t mw =
-                    lane < p.mwp ? reinterpret_cast<const uint32_t *>(dat + h.off_mask)[warp * p.mwp + lane] : 0u;
+                const int32_t *idx_s = reinterpret_cast<const int32_t *>(slot);
+                const unsigned char *val_s = slot + p.off_val;
+                const uint32_t *mask_s = reinterpret_cast<const uint32_t *>(slot + p.off_mask);
+                const XT *x_s = reinterpret_cast<const XT *>(slot + p.off_x);
+                const uint32_t mw = lane < p.mwp ? mask_s[lane] : 0u;
 
                 // running sum of the open segment: compensated (hi + lo) in the accumulation type
                 AT chi[KB], clo[KB];
@@ -357,7 +321,7 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                             cc += (hb >> e) & 1u;
                             if ((vm >> e) & 1u) {
                                 const int ce = FAST ? cc : col_search(p0 + e);
-                                const XT xv = win ? x_s[ce - h.xbase] : static_cast<const XT *>(p.vin[1])[ce];
+                                const XT xv = win ? x_s[ce - xbase] : static_cast<const XT *>(p.vin[1])[ce];
                                 AT mv;
                                 if constexpr (SMEMV) {
                                     mv = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e]]);
@@ -437,7 +401,7 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                     constexpr bool WHOLE = decltype(full_tag)::value;
                     auto xval = [&](int b, int ce) -> AT {
                         if constexpr (WIN) {
-                            return static_cast<AT>(x_s[b * p.x_cap + ce - h.xbase]);
+                            return static_cast<AT>(x_s[b * p.x_cap + ce - xbase]);
                         } else {
                             return static_cast<AT>(static_cast<const XT *>(p.vin[b])[ce]);
                         }
@@ -450,7 +414,6 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                                       static_cast<double>(contrib));
                         }
                     };
-                    const uint32_t *mask_s = reinterpret_cast<const uint32_t *>(dat + h.off_mask) + warp * p.mwp;
                     const VT *vv = reinterpret_cast<const VT *>(val_s);
                     const uint32_t lane_le = FULL >> (31 - lane);  // bits 0..lane
                     const int nsteps = (rel_hi + 255) >> 8;
@@ -697,7 +660,6 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                         run_segdot8(BoolC<true>{}, BoolC<true>{});
                     else
                         run_segdot8(BoolC<true>{}, BoolC<false>{});
-                    fence_proxy_async_smem();  // the scratch writes precede the next bulk copy into this stage
                     // a segment whose end event lies in this tile is complete; the open one
                     // continues in the next tile: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
@@ -731,12 +693,25 @@ __global__ void __launch_bounds__(((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) + 1) * 3
                         run_steps4(BoolC<false>{});
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);  // this warp is done with the stage
-            if (++s == S) {
-                s = 0;
-                ph ^= 1u;
+        }
+        // the slot is free: the tile S ahead goes into it.  Its reads have all returned
+        // (their values were used); the segmented mode also wrote its scratch into the
+        // slot, which the proxy fence orders before the bulk copy's writes.
+        __syncwarp();
+        if constexpr (MODE == MODE_SEGDOT) fence_proxy_async_smem();
+        const int kn = k + S;
+        if (kn < nk) {
+            if ((kn >> 5) == cb + 2) {
+                dcur = dnxt;
+                ecur = enxt;
+                ++cb;
+                load_batch(cb + 1, dnxt, enxt);
             }
+            issue(kn, s);
+        }
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
         }
     }
 
