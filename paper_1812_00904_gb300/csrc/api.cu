@@ -100,7 +100,7 @@ StreamParams base_params(const spmv_plan_s *p) {
 // Layout of one warp's staging slot: indices, values, segment-start masks and, for
 // the scatter and gradient modes, the long-vector windows (16-byte aligned).
 struct SlotGeom {
-    int off_val, off_mask, off_x, bytes;
+    int off_val, off_mask, off_x, off_hdr, bytes;
 };
 SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     SlotGeom g;
@@ -108,7 +108,8 @@ SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
     g.off_x = g.off_mask + (int)align_up((size_t)p->mwp * 4, 16);
     const int nx = mode == MODE_SEGDOT ? 0 : mode == MODE_DVALUES ? 1 : kbt;
-    g.bytes = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 128);
+    g.off_hdr = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 16);  // 32-byte tile header
+    g.bytes = (int)align_up((size_t)g.off_hdr + 32, 128);
     return g;
 }
 // On-chip short-vector bytes of a pass (accumulator of the scatter mode, input otherwise).
@@ -136,6 +137,7 @@ void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt) {
     a.sp.off_val = g.off_val;
     a.sp.off_mask = g.off_mask;
     a.sp.off_x = g.off_x;
+    a.sp.off_hdr = g.off_hdr;
     a.smem = a.sp.vec_region_bytes + BAR_BYTES + W * p->S * g.bytes;
     a.grid = p->ctas;
     a.block = W * 32;

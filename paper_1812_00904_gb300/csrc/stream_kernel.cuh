@@ -189,8 +189,13 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 copy_elem(dst + (size_t)(e - e0) * c_es, c_src + (size_t)e * c_es, c_es);
         }
         const uint32_t total = __reduce_add_sync(FULL, bytes);
+        if (lane == 0) {  // the tile's header, read by this warp when it processes the tile
+            int4 *hd = reinterpret_cast<int4 *>(myslots + (size_t)s * p.stage_bytes + p.off_hdr);
+            hd[0] = d;
+            hd[1] = make_int4(e1, xbase, nxc, 0);
+        }
         __syncwarp();
-        // releases the plain stores; the bulk bytes complete the phase
+        // releases the header and the plain stores; the bulk bytes complete the phase
         if (lane == 0) mbar_arrive_expect_tx(&myfull[s], total);
         if (bytes) bulk_g2s(dst, c_src + (size_t)e0 * c_es, bytes, &myfull[s]);
     };
@@ -212,9 +217,10 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
             }
             break;
         }
-        int4 d;
-        int e1;
-        desc(k, d, e1);
+        // tile header: first nonzero, first owned end event, flags, next tile's first
+        // nonzero; next tile's first end event, long-vector window base and length
+        const int4 d = reinterpret_cast<const int4 *>(slot + p.off_hdr)[0];
+        const int4 d1 = reinterpret_cast<const int4 *>(slot + p.off_hdr)[1];
         const int kb0 = d.x & ~7;
         const int ncov = ((d.w + 7) & ~7) - kb0;
         if (ncov < 0 || ncov > p.tile_cap) {
@@ -222,13 +228,12 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
         } else {
             {
                 const int t = ta + warp + k * W;
-                const int i0 = d.y, i1 = e1;
+                const int i0 = d.y, i1 = d1.x;
                 const bool needLeft = (d.z & 1) != 0;
                 const bool needRight = (d.z & 2) != 0;
                 const bool dup = (d.z & 4) != 0;
-                int xbase, nxc;
-                xwindow(i0, i1, xbase, nxc);
-                const bool win = nxc <= p.x_cap;
+                const int xbase = d1.y;
+                const bool win = d1.z <= p.x_cap;
                 const int rel_lo = d.x - kb0;
                 const int rel_hi = d.w - kb0;
                 const bool full = rel_lo == 0 && (rel_hi & 255) == 0;  // whole 256-position steps only
