@@ -253,6 +253,46 @@ def time_pair_gbs(pkg, plan, m, n, nnz, layout, steps, sv=4, stream=None):
             "frac_of_hbm_peak": round(b / (ms / 1e3) / 1e9 / load_peaks()[0], 4)}
 
 
+def small_fp64_flushed(pkg, dev, reps: int = 50):
+    """The m=1,000 x n=100,000 FP64 wide matrix (about 0.5M nonzeros, L2-sized): each SpMV and
+    SpVTM timed alone with a 256 MB buffer written between repetitions to flush L2."""
+    import torch
+
+    import synth
+
+    A = synth.wide_fp64_small(0)
+    ptr = torch.from_numpy(A.ptr.astype("int32")).to(dev)
+    idx = torch.from_numpy(A.idx.astype("int32")).to(dev)
+    vals = torch.from_numpy(A.vals).to(dev)
+    plan = pkg.Plan(A.m, A.n, ptr, idx, vals, layout="csc")
+    g = torch.Generator(device=dev)
+    g.manual_seed(15)
+    x = torch.rand(A.n, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+    v = torch.rand(A.m, generator=g, device=dev, dtype=torch.float64) * 2 - 1
+    y = torch.empty(A.m, device=dev, dtype=torch.float64)
+    u = torch.empty(A.n, device=dev, dtype=torch.float64)
+    flush = torch.empty(64 << 20, device=dev, dtype=torch.float32)  # 256 MB > L2
+    res = {}
+    for name, fn in (("spmv", lambda: pkg.spmv(plan.handle, x, y)), ("spvtm", lambda: pkg.spvtm(plan.handle, v, u))):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        b = A.nnz * 12 + (A.n + 1) * 4 + (A.n + A.m) * 8
+        res[name] = {"ms_median": round(ms, 4), "ms_min": round(min(ts), 4), "gbs": round(b / (ms / 1e3) / 1e9, 1)}
+    plan.check()
+    plan.close()
+    res.update(workload="wide_csc_m1000_n100000_fp64_zipf2_5dense", nnz=int(A.nnz), l2="flushed between repetitions")
+    return res
+
+
 def batched_rate(pkg, plan, m, n, nnz, k, steps):
     """Vectors/s and effective GB/s of k-vector SpMV and SpVTM passes (matrix streamed once per pass)."""
     import torch
@@ -480,6 +520,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.skip_extras:
         extras = {}
         extras["batched_k8"] = batched_rate(pkg, plan, m, n, nnz, 8, max(10, args.steps // 20))
+        extras["wide_fp64_small"] = small_fp64_flushed(pkg, dev)
         vb = A.vals.to(torch.bfloat16)
         pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32)
         extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),

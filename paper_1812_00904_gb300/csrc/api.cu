@@ -384,7 +384,15 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     smem_max -= 1024;  // static shared memory and slack
 
     // ---- launch configuration: tiles of T nonzeros, rounds of W tiles, S stages per CTA
-    p->T = (opts && opts->tile_items) ? opts->tile_items : 512;
+    // default tile: 512 nonzeros (two whole 256-position steps); smaller when the matrix has
+    // too few nonzeros to give every warp of a full wave about two tiles
+    p->T = 512;
+    if (opts && opts->tile_items) {
+        p->T = opts->tile_items;
+    } else {
+        const int64_t fill = (int64_t)sms * 16 * 2;
+        if (nnz < fill * 512) p->T = (int)std::max<int64_t>(64, std::min<int64_t>(512, (nnz / fill) & ~int64_t(7)));
+    }
     p->S = (opts && opts->stages) ? opts->stages : 2;
     int W = (opts && opts->warps_per_cta) ? opts->warps_per_cta : MAX_WARPS;
     if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)

@@ -376,6 +376,16 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                     if (WHOLE || vm_r) {
                         stag8_idx(idx_s, p0, sw, ix);
                         Stag8<VT, AT>::run(val_s, p0, sw, va);
+                        if (!WHOLE) {
+                            // positions outside the tile hold whatever the slot held before:
+                            // zero them (a stale NaN or infinity times zero would not vanish)
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                if (!((vm_r >> e) & 1u)) {
+                                    ix[e] = 0;
+                                    va[e] = AT(0);
+                                }
+                        }
                         unsigned mx = 0;
 #pragma unroll
                         for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(ix[e]));

@@ -142,3 +142,24 @@ def test_autograd_least_squares_wide_fp64_workload(dtype):
     fd = float(lp - lm) / (2 * h)
     an = float((x.grad * d).sum())
     assert abs(fd - an) <= 1e-2 * max(1.0, abs(an))
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+@pytest.mark.parametrize("tile_items", [0, 40, 104, 256])
+@pytest.mark.parametrize("k", [2, 3, 8])
+def test_batch_small_tiles_match_single_vector_calls(layout, tile_items, k):
+    """Multi-vector passes over small tiles (partial steps, many zones) equal the single-vector calls."""
+    m, n = (900, 25_000) if layout == "csc" else (25_000, 900)
+    A = synth.random_matrix(m, n, layout, density=0.01, seed=2)
+    plan, stored = make_plan(A, torch.float32, tile_items=tile_items)
+    X = torch.stack([dev_vec(synth.uniform_vector(n, 300 + b), torch.float32) for b in range(k)])
+    V = torch.stack([dev_vec(synth.uniform_vector(m, 400 + b), torch.float32) for b in range(k)])
+    Y = plan.batch(pkg.SPMV_OP_AX, X)
+    U = plan.batch(pkg.SPMV_OP_VTA, V)
+    plan.check()
+    for b in range(k):
+        xs, vs = host_of(X[b]), host_of(V[b])
+        assert_close(host_of(Y[b]), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, f"Y[{b}]")
+        assert_close(host_of(U[b]), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, f"U[{b}]")
+    seg_single = plan.spvtm(V[k - 1]) if layout == "csc" else plan.spmv(X[k - 1])
+    assert torch.equal(seg_single, U[k - 1] if layout == "csc" else Y[k - 1])

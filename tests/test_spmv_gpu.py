@@ -264,3 +264,28 @@ def test_wide_fp64_workload_matches_oracle():
     check_products(plan, stored, synth.uniform_vector(A.n, 100), synth.uniform_vector(A.m, 101), 1e-12, "wide fp64")
     info = plan.info()
     assert info["imbalance"] * A.nnz / info["chunks"] <= 1.0  # chunk sizes differ by at most one (Sec. II)
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+def test_stale_slot_contents_do_not_leak(layout):
+    """A partial last step reads slot positions past the tile's end: whatever a previous launch
+    left there (here: infinities and NaNs of a matrix that holds only those) must not reach the
+    sums of the next launch."""
+    m, n = (25_000, 900) if layout == "csr" else (900, 25_000)
+    A = synth.random_matrix(m, n, layout, density=0.01, seed=2)
+    t, stored = device_matrix(A, torch.float32)
+    poison = torch.full_like(t["vals"], float("inf"))
+    poison[::2] = float("nan")
+    bad = pkg.Plan(m, n, t["ptr"], t["idx"], poison, layout=layout, tile_items=64)
+    good = pkg.Plan(m, n, t["ptr"], t["idx"], t["vals"], layout=layout, tile_items=64)
+    x = dev_vec(synth.uniform_vector(n, 1), torch.float32)
+    v = dev_vec(synth.uniform_vector(m, 2), torch.float32)
+    for _ in range(3):
+        bad.spmv(x)
+        bad.spvtm(v)
+        y = host_of(good.spmv(x))
+        u = host_of(good.spvtm(v))
+        xs, vs = host_of(x), host_of(v)
+        assert_close(y, oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, "y after a poisoned launch")
+        assert_close(u, oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, "u after a poisoned launch")
+    good.check()
