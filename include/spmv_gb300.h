@@ -75,7 +75,9 @@ typedef enum { SPMV_OP_AX = 0, SPMV_OP_VTA = 1 } spmv_op;                       
 typedef struct spmv_plan_s *spmv_plan_t;
 
 /* Plan flags. */
-#define SPMV_PLAN_NO_VALIDATE 0x1u  /* skip the structural checks of ptr/idx */
+#define SPMV_PLAN_NO_VALIDATE 0x1u  /* skip the structural checks of ptr/idx at plan time; the kernels then
+                                       check every index (an out-of-range one is clamped and reported by
+                                       spmv_check).  A validated plan relies on idx staying unchanged. */
 #define SPMV_PLAN_PROFILE 0x2u      /* time every kernel launch with CUDA events (spmv_profile_read) */
 #define SPMV_PLAN_SHORT_IN_GLOBAL 0x4u /* keep the short vector in global memory even when it fits on chip */
 

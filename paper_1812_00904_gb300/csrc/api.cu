@@ -91,6 +91,7 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.stages = p->S;
     sp.x_cap = p->x_cap;
     sp.tile_cap = p->T;
+    sp.checked = (p->flags & SPMV_PLAN_NO_VALIDATE) ? 1 : 0;
     sp.rec_left = p->rec_left;
     sp.rec_right = p->rec_right;
     sp.err = p->err;
@@ -350,6 +351,8 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         return set_error(SPMV_ERR_UNSUPPORTED, "supported (values, vectors): (f64,f64) (f32,f32) (bf16,f32) (f16,f32)");
     if (!ptr) return set_error(SPMV_ERR_INVALID_ARG, "ptr is NULL");
     if (nnz > 0 && (!idx || !vals)) return set_error(SPMV_ERR_INVALID_ARG, "idx/vals are NULL");
+    if (nnz > 0 && (layout == SPMV_CSC_WIDE ? m : n) == 0)
+        return set_error(SPMV_ERR_BAD_MATRIX, "nonzeros need a nonempty indexed dimension");
     if (!aligned16(ptr) || (nnz > 0 && (!aligned16(idx) || !aligned16(vals))))
         return set_error(SPMV_ERR_INVALID_ARG, "ptr, idx and vals must be 16-byte aligned device pointers");
     for (const void *q : {(const void *)ptr, (const void *)idx, vals}) {

@@ -242,6 +242,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 const uint32_t *mask_s = reinterpret_cast<const uint32_t *>(slot + p.off_mask);
                 const XT *x_s = reinterpret_cast<const XT *>(slot + p.off_x);
                 const uint32_t mw = lane < p.mwp ? mask_s[lane] : 0u;
+                bool idx_bad = false;  // an index outside the short vector was met in this tile
 
                 // running sum of the open segment: compensated (hi + lo) in the accumulation type
                 AT chi[KB], clo[KB];
@@ -364,8 +365,9 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 };
                 // indices and values of the lane's 8 positions (register order); returns the
                 // register-order valid bits with out-of-range indices removed (and reported)
-                auto step_load = [&](auto full_tag, int p0, uint32_t vm_r, int (&ix)[8], AT (&va)[8]) -> uint32_t {
+                auto step_load = [&](auto full_tag, auto check_tag, int p0, uint32_t vm_r, int (&ix)[8], AT (&va)[8]) -> uint32_t {
                     constexpr bool WHOLE = decltype(full_tag)::value;
+                    constexpr bool CHECK = decltype(check_tag)::value;
                     if (!WHOLE) {
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
@@ -386,21 +388,18 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                                     va[e] = AT(0);
                                 }
                         }
-                        unsigned mx = 0;
+                        // out-of-range indices are clamped into the vector (never dereferenced
+                        // outside it) and reported once per tile; a plan whose indices were
+                        // validated skips this on its whole steps (the indices are borrowed
+                        // unchanged)
+                        if constexpr (CHECK) {
+                            unsigned mx = 0;
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(ix[e]));
-                        if (mx >= n_minor) {
-                            uint32_t bad = 0;
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) bad |= (static_cast<unsigned>(ix[e]) >= n_minor ? 1u : 0u) << e;
-                            if (bad & vm_r) atomicOr(p.err, ERR_INDEX);  // out-of-range entries are skipped
-                            vm_r &= ~bad;
-#pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                if ((bad >> e) & 1u) {
-                                    ix[e] = 0;
-                                    va[e] = AT(0);
-                                }
+                            for (int e = 0; e < 8; ++e) {
+                                mx = max(mx, static_cast<unsigned>(ix[e]));
+                                ix[e] = static_cast<int>(min(static_cast<unsigned>(ix[e]), n_minor - 1u));
+                            }
+                            idx_bad |= mx >= n_minor;
                         }
                     }
                     return vm_r;
@@ -410,7 +409,8 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 // Consecutive lanes hold consecutive positions, whose rows (sorted within a
                 // column) fall in different shared-memory banks far more often than the rows
                 // of positions 8 apart: fewer conflicted atomic wavefronts.
-                auto run_scatter = [&](auto fast_tag, auto win_tag, auto full_tag) {
+                auto run_scatter = [&](auto fast_tag, auto win_tag, auto full_tag, auto check_tag) {
+                    constexpr bool CHECK = decltype(check_tag)::value;
                     constexpr bool FAST = decltype(fast_tag)::value;
                     constexpr bool WIN = decltype(win_tag)::value;
                     constexpr bool WHOLE = decltype(full_tag)::value;
@@ -464,20 +464,15 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                                 ok &= ~(1u << e);
                             }
                         }
-                        {
+                        if constexpr (CHECK) {
+                            // out-of-range rows are clamped into the accumulator and reported
                             unsigned mx = 0;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) mx = max(mx, static_cast<unsigned>(row[e]));
-                            if (mx >= n_minor) {  // out-of-range entries are skipped and reported
-#pragma unroll
-                                for (int e = 0; e < 8; ++e)
-                                    if (static_cast<unsigned>(row[e]) >= n_minor) {
-                                        if ((ok >> e) & 1u) atomicOr(p.err, ERR_INDEX);
-                                        ok &= ~(1u << e);
-                                        row[e] = 0;
-                                        a[e] = AT(0);
-                                    }
+                            for (int e = 0; e < 8; ++e) {
+                                mx = max(mx, static_cast<unsigned>(row[e]));
+                                row[e] = static_cast<int>(min(static_cast<unsigned>(row[e]), n_minor - 1u));
                             }
+                            idx_bad |= mx >= n_minor;
                         }
                         if (FAST && (w[0] | w[1] | w[2] | w[3] | w[4] | w[5] | w[6] | w[7]) == 0u) {
                             // no segment starts in this step: every position is in segment i0 + cb
@@ -522,13 +517,14 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                                                 : reinterpret_cast<AT *>(const_cast<int32_t *>(idx_s));
                 // front of a step: segment-start bits, loads, products and the lane-local
                 // inclusive prefix rr (position order, restarted at every head)
-                auto seg_front = [&](auto full_tag, int stp, int &p0, uint32_t &hb, int &base, AT (&rr)[8][KB]) {
+                auto seg_front = [&](auto full_tag, auto check_tag, int stp, int &p0, uint32_t &hb, int &base,
+                                     AT (&rr)[8][KB]) {
                     constexpr bool WHOLE = decltype(full_tag)::value;
                     uint32_t vm;
                     step_head(full_tag, stp, p0, hb, base, vm);
                     int ix[8];
                     AT va[8];
-                    const uint32_t vm_r = step_load(full_tag, p0, rot4(vm, sw), ix, va);
+                    const uint32_t vm_r = step_load(full_tag, check_tag, p0, rot4(vm, sw), ix, va);
 #pragma unroll
                     for (int b = 0; b < KB; ++b) {
                         AT pr[8];
@@ -608,7 +604,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                         chi[b] = s_;
                     }
                 };
-                // the open segment runs through a whole head-free step (or pair): add its total
+                // the open segment runs through a whole head-free step: add its total
                 auto seg_carry_total = [&](int b, AT t) {
 #pragma unroll
                     for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
@@ -617,42 +613,13 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                     clo[b] += (chi[b] - (s_ - bp)) + (t - bp);
                     chi[b] = s_;
                 };
-                auto run_segdot8 = [&](auto fast_tag, auto full_tag) {
-                    constexpr bool WHOLE = decltype(full_tag)::value;
+                auto run_segdot8 = [&](auto fast_tag, auto full_tag, auto check_tag) {
                     const int nsteps = (rel_hi + 255) >> 8;
-                    int stp = 0;
-                    if constexpr (WHOLE && KB <= 2) {
-                        // two steps at a time: their fronts and scans are independent and interleave
-                        for (; stp + 1 < nsteps; stp += 2) {
-                            int p0a, p0b, basea, baseb;
-                            uint32_t hba, hbb;
-                            AT rra[8][KB], rrb[8][KB];
-                            seg_front(full_tag, stp, p0a, hba, basea, rra);
-                            seg_front(full_tag, stp + 1, p0b, hbb, baseb, rrb);
-                            const unsigned bala = __ballot_sync(FULL, hba != 0u);
-                            const unsigned balb = __ballot_sync(FULL, hbb != 0u);
-                            if ((bala | balb) == 0u) {
-#pragma unroll
-                                for (int b = 0; b < KB; ++b) seg_carry_total(b, rra[7][b] + rrb[7][b]);
-                                continue;
-                            }
-#pragma unroll
-                            for (int b = 0; b < KB; ++b) {
-                                AT Texa, Texb;
-                                const AT Ta = seg_scan(bala, rra[7][b], Texa);
-                                const AT Tb = seg_scan(balb, rrb[7][b], Texb);
-                                const AT T31a = __shfl_sync(FULL, Ta, 31);
-                                const AT T31b = __shfl_sync(FULL, Tb, 31);
-                                seg_back(fast_tag, b, bala, p0a, hba, basea, rra, Texa, T31a);
-                                seg_back(fast_tag, b, balb, p0b, hbb, baseb, rrb, Texb, T31b);
-                            }
-                        }
-                    }
-                    for (; stp < nsteps; ++stp) {
+                    for (int stp = 0; stp < nsteps; ++stp) {
                         int p0, base;
                         uint32_t hb;
                         AT rr[8][KB];
-                        seg_front(full_tag, stp, p0, hb, base, rr);
+                        seg_front(full_tag, check_tag, stp, p0, hb, base, rr);
                         const unsigned bal = __ballot_sync(FULL, hb != 0u);
                         if (bal == 0u) {
 #pragma unroll
@@ -670,11 +637,11 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
 
                 if constexpr (MODE == MODE_SEGDOT) {
                     if (dup)
-                        run_segdot8(BoolC<false>{}, BoolC<false>{});
-                    else if (full)
-                        run_segdot8(BoolC<true>{}, BoolC<true>{});
+                        run_segdot8(BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
+                    else if (full && !p.checked)
+                        run_segdot8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
                     else
-                        run_segdot8(BoolC<true>{}, BoolC<false>{});
+                        run_segdot8(BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
                     // a segment whose end event lies in this tile is complete; the open one
                     // continues in the next tile: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
@@ -690,16 +657,16 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 } else if constexpr (MODE == MODE_SCATTER) {
                     if (win) {
                         if (dup)
-                            run_scatter(BoolC<false>{}, BoolC<true>{}, BoolC<false>{});
-                        else if (full)
-                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{});
+                            run_scatter(BoolC<false>{}, BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
+                        else if (full && !p.checked)
+                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
                         else
-                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
                     } else {
                         if (dup)
-                            run_scatter(BoolC<false>{}, BoolC<false>{}, BoolC<false>{});
+                            run_scatter(BoolC<false>{}, BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
                         else
-                            run_scatter(BoolC<true>{}, BoolC<false>{}, BoolC<false>{});
+                            run_scatter(BoolC<true>{}, BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
                     }
                 } else {
                     if (!dup)
@@ -707,6 +674,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                     else
                         run_steps4(BoolC<false>{});
                 }
+                if (__any_sync(FULL, idx_bad) && lane == 0) atomicOr(p.err, ERR_INDEX);
             }
         }
         // the slot is free: the tile S ahead goes into it.  Its reads have all returned
