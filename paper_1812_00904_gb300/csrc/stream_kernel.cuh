@@ -54,6 +54,9 @@ __device__ __forceinline__ double2 make_pair2(double a, double b) { return make_
 template <bool B> struct BoolC {
     static constexpr bool value = B;
 };
+struct RtBool {  // a flag known only at run time, passed where a BoolC may be
+    bool value;
+};
 
 template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
 __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
 
                 // ---- DVALUES: 4 consecutive positions per lane, 128 per step
                 auto run_steps4 = [&](auto fast_tag) {
-                    constexpr bool FAST = decltype(fast_tag)::value;
+                    const bool FAST = fast_tag.value;  // compile-time (BoolC) or run-time (RtBool)
                     const int nsteps = (rel_hi + 127) >> 7;
 #pragma unroll 2
                     for (int stp = 0; stp < nsteps; ++stp) {
@@ -411,7 +414,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 // of positions 8 apart: fewer conflicted atomic wavefronts.
                 auto run_scatter = [&](auto fast_tag, auto win_tag, auto full_tag, auto check_tag) {
                     constexpr bool CHECK = decltype(check_tag)::value;
-                    constexpr bool FAST = decltype(fast_tag)::value;
+                    const bool FAST = fast_tag.value;  // compile-time (BoolC) or run-time (RtBool)
                     constexpr bool WIN = decltype(win_tag)::value;
                     constexpr bool WHOLE = decltype(full_tag)::value;
                     auto xval = [&](int b, int ce) -> AT {
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 // carry the open sum at the end of the step (T31) into (chi, clo)
                 auto seg_back = [&](auto fast_tag, int b, unsigned bal, int p0, uint32_t hb, int base,
                                     const AT (&rr)[8][KB], AT Tex, AT T31) {
-                    constexpr bool FAST = decltype(fast_tag)::value;
+                    const bool FAST = fast_tag.value;  // compile-time (BoolC) or run-time (RtBool)
                     if (hb != 0u && b < kb) {
                         AT *ev = ev_base + p0;
                         // value closing at position e: the open sum up to e - 1 (0 at e = 0)
@@ -636,12 +639,10 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                 };
 
                 if constexpr (MODE == MODE_SEGDOT) {
-                    if (dup)
-                        run_segdot8(BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
-                    else if (full && !p.checked)
+                    if (full && !dup && !p.checked)
                         run_segdot8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
                     else
-                        run_segdot8(BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
+                        run_segdot8(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
                     // a segment whose end event lies in this tile is complete; the open one
                     // continues in the next tile: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
@@ -655,24 +656,14 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
                         }
                     }
                 } else if constexpr (MODE == MODE_SCATTER) {
-                    if (win) {
-                        if (dup)
-                            run_scatter(BoolC<false>{}, BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
-                        else if (full && !p.checked)
-                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
-                        else
-                            run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
-                    } else {
-                        if (dup)
-                            run_scatter(BoolC<false>{}, BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
-                        else
-                            run_scatter(BoolC<true>{}, BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
-                    }
-                } else {
-                    if (!dup)
-                        run_steps4(BoolC<true>{});
+                    if (win && full && !dup && !p.checked)
+                        run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                    else if (win)
+                        run_scatter(RtBool{!dup}, BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
                     else
-                        run_steps4(BoolC<false>{});
+                        run_scatter(RtBool{!dup}, BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
+                } else {
+                    run_steps4(RtBool{!dup});
                 }
                 if (__any_sync(FULL, idx_bad) && lane == 0) atomicOr(p.err, ERR_INDEX);
             }
