@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(COMB_X * COMB_Y) combine_kernel(const PT *__re
 // tile + the records of the middle tiles (whole-tile sums, kept as right records)
 // + left record of the last, added in this order with TwoSum in the accumulation
 // type.  One thread per zone (most zones span two tiles); the loads of a long zone
-// are issued four at a time.  Every zone's column is written once.
+// are issued eight at a time.  Every zone's column is written once.
 template <typename XT, typename T, typename RT>
 __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ zones, int z,
                                                     const RT *__restrict__ rec_left, const RT *__restrict__ rec_right,
@@ -75,12 +75,12 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
         const RT l = rec_left[(size_t)b * P + zd.last];
         T s = f.x, c = f.y;
         int q = zd.first + 1;
-        for (; q + 4 <= zd.last; q += 4) {
-            RT m[4];
+        for (; q + 8 <= zd.last; q += 8) {
+            RT m[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) m[e] = rr[q + e];
+            for (int e = 0; e < 8; ++e) m[e] = rr[q + e];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < 8; ++e) {
                 two_sum_add(s, c, m[e].x);
                 c += m[e].y;
             }
