@@ -521,6 +521,15 @@ def run_ours(args):
         extras = {}
         extras["batched_k8"] = batched_rate(pkg, plan, m, n, nnz, 8, max(10, args.steps // 20))
         extras["wide_fp64_small"] = small_fp64_flushed(pkg, dev)
+        # least squares by CGLS on the same matrix: one SpMV + one SpVTM + vector updates per iteration
+        bl = torch.rand(m, generator=g, device=dev) * 2 - 1
+        xl = torch.zeros(n, device=dev)
+        torch.cuda.synchronize()
+        tc0 = time.perf_counter()
+        it, rel = pkg.spmv_cgls(plan.handle, bl, xl, 50, 0.0)
+        tc = time.perf_counter() - tc0
+        extras["cgls"] = {"iterations": it, "ms_per_iteration": round(tc * 1e3 / max(it, 1), 4),
+                          "rel_grad": rel, "note": "wall clock of the call, including its setup"}
         vb = A.vals.to(torch.bfloat16)
         pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32)
         extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),

@@ -218,6 +218,33 @@ spmv_status spmv_profile_reset(spmv_plan_t plan);
 spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, const int32_t *idx,
                          const float *vals, const float *x, float *y, void *stream);
 
+/*
+ * spmv_normal -- u = A^T (A x), the normal-equation operator of least squares:
+ * one SpMV (Sec. III) whose result feeds one SpVTM (Sec. IV-A), the pairing the
+ * paper measures (Sec. V) with the SpVTM consuming the SpMV's output.
+ *   x (n), u (n): 16-byte aligned device vectors of the plan's vector type; u is overwritten
+ *   y (m): device buffer that receives A x, or NULL (the plan keeps its own, allocated once)
+ * Asynchronous on `stream`.  Errors as for spmv/spvtm.
+ */
+spmv_status spmv_normal(spmv_plan_t plan, const void *x, void *u, void *y, void *stream);
+
+/*
+ * spmv_cgls -- least squares min ||A x - b||_2 by conjugate gradients on the
+ * normal equations (CGLS), the kind of first-order method the SpMV-SpVTM pairs of
+ * the paper serve (Sec. V, Sec. VII); there is no such solver in the paper.  Every
+ * product and vector operation runs on the device; the iteration's scalars stay in
+ * device memory and the host reads them every 8 iterations to stop.
+ *   b (m), x (n)    16-byte aligned device vectors of the plan's vector type; x holds
+ *                   the start on entry (zeros for the minimum-norm solution of an
+ *                   underdetermined problem) and the last iterate on return
+ *   max_iters, tol  stop after max_iters iterations or once ||A^T r|| <= tol ||A^T r_0||
+ *   iters_done, rel_grad  (may be NULL) iterations run and ||A^T r|| / ||A^T r_0||
+ * Synchronizes `stream`; allocates its work vectors (4 vectors and a few scalars)
+ * for the duration of the call.
+ */
+spmv_status spmv_cgls(spmv_plan_t plan, const void *b, void *x, int32_t max_iters, double tol, void *stream,
+                      int32_t *iters_done, double *rel_grad);
+
 /* Thread-local message for the last failing call of this thread ("" if none). */
 const char *spmv_last_error(void);
 

@@ -127,6 +127,33 @@ class Oracle:
         return loss, self.spvtm(A, r), self.dvalues(A, r, x), r
 
 
+    def cgls(self, A, b, x0, iters: int):
+        """CGLS (conjugate gradients on the normal equations A^T A x = A^T b), FP64, from x0.
+
+        Not part of the paper: the least-squares loop its SpMV-SpVTM pairs serve.  The
+        standard recurrences: r = b - A x, s = A^T r, p = s, gamma = s.s; per iteration
+        q = A p, alpha = gamma / q.q, x += alpha p, r -= alpha q, s = A^T r,
+        gamma' = s.s, p = s + (gamma' / gamma) p.  Returns (x, ||s|| / ||s_0||).
+        """
+        x = _f64(x0).copy()
+        r = _f64(b) - self.spmv(A, x)
+        s = self.spvtm(A, r)
+        p = s.copy()
+        gamma0 = gamma = float(np.dot(s, s))
+        for _ in range(iters):
+            q = self.spmv(A, p)
+            delta = float(np.dot(q, q))
+            alpha = gamma / delta if delta > 0.0 else 0.0
+            x += alpha * p
+            r -= alpha * q
+            s = self.spvtm(A, r)
+            gamma_new = float(np.dot(s, s))
+            beta = gamma_new / gamma if gamma > 0.0 else 0.0
+            gamma = gamma_new
+            p = s + beta * p
+        return x, (np.sqrt(gamma / gamma0) if gamma0 > 0.0 else 0.0)
+
+
 _default = None
 
 
@@ -151,6 +178,10 @@ def dvalues(A, r, x):
 
 def least_squares(A, x, b):
     return _get().least_squares(A, x, b)
+
+
+def cgls(A, b, x0, iters):
+    return _get().cgls(A, b, x0, iters)
 
 
 def abs_spmv(A, x):

@@ -16,7 +16,7 @@ from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, 
 
 __all__ = [
     "spmv_plan", "spmv_plan_ex", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
-    "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
+    "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_normal", "spmv_cgls", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
     "spmv_version", "serve_create", "serve_register", "serve_register_host", "serve_submit", "serve_poll",
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
     "SPMV_CSC_WIDE", "SPMV_CSR_TALL", "SPMV_F64", "SPMV_F32", "SPMV_BF16", "SPMV_F16", "SPMV_OP_AX", "SPMV_OP_VTA",
@@ -126,6 +126,20 @@ def spmv_profile_reset(plan):
 def spmv_noalloc(m, n, nnz, ptr, idx, vals, x, y, stream=None):
     """y = A x (wide CSC, FP32) with no device allocation: scratch in the library's static device memory."""
     _lib.call("spmv_noalloc", m, n, nnz, _addr(ptr), _addr(idx), _addr(vals), _addr(x), _addr(y), _stream(stream))
+
+
+def spmv_normal(plan, x, u, y=None, stream=None):
+    """u = A^T (A x); y (optional) receives A x."""
+    _lib.call("spmv_normal", plan, _addr(x), _addr(u), _addr(y), _stream(stream))
+
+
+def spmv_cgls(plan, b, x, max_iters, tol, stream=None):
+    """Least squares by CGLS on the device; x is updated in place.  Returns (iterations, ||A^T r|| / ||A^T r0||)."""
+    it = ctypes.c_int32()
+    rel = ctypes.c_double()
+    _lib.call("spmv_cgls", plan, _addr(b), _addr(x), int(max_iters), float(tol), _stream(stream), ctypes.byref(it),
+              ctypes.byref(rel))
+    return it.value, rel.value
 
 
 def spmv_last_error() -> str:
@@ -250,6 +264,18 @@ class Plan:
         g = torch.empty(self.nnz, dtype=self.val_dtype, device=self.vals.device) if out is None else out
         spmv_dvalues(self.handle, r, x, g, stream)
         return g
+
+    def normal(self, x, out=None, stream=None):
+        """A^T (A x)."""
+        u = self._empty(self.n) if out is None else out
+        spmv_normal(self.handle, x, u, None, stream)
+        return u
+
+    def cgls(self, b, x0=None, max_iters=100, tol=1e-6, stream=None):
+        """Least squares min ||A x - b|| from x0 (zeros by default); returns (x, iterations, relative gradient)."""
+        x = self._empty(self.n).zero_() if x0 is None else x0.clone()
+        it, rel = spmv_cgls(self.handle, b, x, max_iters, tol, stream)
+        return x, it, rel
 
     def info(self) -> dict:
         return spmv_plan_info(self.handle)

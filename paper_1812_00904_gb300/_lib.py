@@ -87,6 +87,8 @@ SIGNATURES = {
     "spmv_profile_read": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "spmv_profile_reset": (_I32, [_P]),
     "spmv_noalloc": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P]),
+    "spmv_normal": (_I32, [_P, _P, _P, _P, _P]),
+    "spmv_cgls": (_I32, [_P, _P, _P, _I32, ctypes.c_double, _P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double)]),
     "spmv_last_error": (ctypes.c_char_p, []),
     "spmv_version": (ctypes.c_char_p, []),
     "serve_create": (_I32, [ctypes.POINTER(_P), _U64, _I32, _I32]),

@@ -281,6 +281,7 @@ void free_plan(spmv_plan_s *p) {
     if (p->hin) cudaFree(p->hin);
     if (p->hout) cudaFree(p->hout);
     if (p->hg) cudaFree(p->hg);
+    if (p->ynorm) cudaFree(p->ynorm);
     delete p;
 }
 
@@ -683,7 +684,7 @@ spmv_status spmv_check(spmv_plan_t p, void *stream) {
     if (e) {
         CUDA_TRY(cudaMemset(p->err, 0, 4));
         std::string msg = "device error:";
-        if (e & 1) msg += " index outside the short vector (entry skipped);";
+        if (e & 1) msg += " index outside the short vector (clamped into it);";
         if (e & 2) msg += " staging wait timed out;";
         if (e & 4) msg += " inconsistent tile descriptor;";
         return set_error(SPMV_ERR_DEVICE, msg);

@@ -51,6 +51,7 @@ struct spmv_plan_s {
     // staging buffers for host-pointer calls (allocated on first use)
     std::mutex host_mu;
     void *hin = nullptr, *hout = nullptr, *hg = nullptr;
+    void *ynorm = nullptr;  // A x of spmv_normal when the caller passes no buffer
 
     // kernel timers (SPMV_PLAN_PROFILE)
     struct Prof {

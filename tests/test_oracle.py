@@ -7,7 +7,9 @@ import zlib
 import numpy as np
 import pytest
 
+import oracle
 import pins
+import synth
 from oracle import plan as plan_oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_example.json")
@@ -134,3 +136,23 @@ def test_plan_rules_match_brute_force(kind):
                 assert po.needRight[S[0]] == 1 and po.rightGroup[S[0]] == k
                 assert po.procsOnRight[S[0]] == len(S) - 1
                 assert all(po.jf[p] == j or po.jl[p] == j for p in S)
+
+
+@pytest.mark.parametrize("shape", [(60, 12), (12, 60)])
+def test_oracle_cgls_reaches_the_least_squares_solution(shape):
+    """CGLS from zero converges to the least-squares solution of a tall full-rank problem and to
+    the minimum-norm solution of a wide one (both given by numpy's lstsq)."""
+    m, n = shape
+    layout = "csr" if m > n else "csc"
+    A = synth.random_matrix(m, n, layout, density=0.5, seed=31)
+    b = synth.uniform_vector(m, 32)
+    D = pins.dense_of(A)
+    x_ref = np.linalg.lstsq(D, b, rcond=None)[0]
+    x, rel = oracle.cgls(A, b, np.zeros(n), iters=4 * min(m, n))
+    assert rel < 1e-8
+    assert np.allclose(x, x_ref, rtol=1e-7, atol=1e-9 * np.abs(x_ref).max())
+    # one step from zero is the steepest-descent step on the normal equations
+    g = D.T @ b
+    alpha = g @ g / np.sum((D @ g) ** 2)
+    x1, _ = oracle.cgls(A, b, np.zeros(n), iters=1)
+    assert np.allclose(x1, alpha * g, rtol=1e-12, atol=1e-15)
