@@ -140,6 +140,20 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
                          int32_t val_dtype, int32_t vec_dtype, void *stream, uint32_t flags,
                          const spmv_plan_opts *opts);
 
+/*
+ * spmv_plan_coo -- a plan from coordinate triples in storage order: sorted by
+ * column for SPMV_CSC_WIDE (the column-major triple stream of Sec. V), by row for
+ * SPMV_CSR_TALL; order inside a column (row) is free and repeated (i, j) add up.
+ *   rows, cols (nnz int32 each), vals (nnz, val_dtype): device arrays, BORROWED like
+ *   idx/vals of spmv_plan (the minor indices serve as idx); the plan builds and owns
+ *   the pointer array on the device.  Other arguments as for spmv_plan_ex.
+ * Synchronizes `stream` once.  Errors: SPMV_ERR_BAD_MATRIX when a major index is out
+ * of range or the stream is not sorted by it, then the errors of spmv_plan_ex.
+ */
+spmv_status spmv_plan_coo(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout,
+                          const int32_t *rows, const int32_t *cols, const void *vals, int32_t val_dtype,
+                          int32_t vec_dtype, void *stream, uint32_t flags, const spmv_plan_opts *opts);
+
 /* Release the plan's workspace.  Accepts NULL.  The caller's arrays are untouched. */
 spmv_status spmv_plan_destroy(spmv_plan_t plan);
 

@@ -15,7 +15,7 @@ from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, 
                    SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL, SpmvError)
 
 __all__ = [
-    "spmv_plan", "spmv_plan_ex", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
+    "spmv_plan", "spmv_plan_ex", "spmv_plan_coo", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
     "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_normal", "spmv_cgls", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
     "spmv_version", "serve_create", "serve_register", "serve_register_host", "serve_submit", "serve_poll",
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
@@ -72,6 +72,15 @@ def spmv_plan_ex(m, n, nnz, layout, ptr, idx, vals, val_dtype, vec_dtype, stream
     h = ctypes.c_void_p()
     opts = _lib.spmv_plan_opts(chunks, warps_per_cta, tile_items, stages)
     _lib.call("spmv_plan_ex", ctypes.byref(h), m, n, nnz, layout, _addr(ptr), _addr(idx), _addr(vals), val_dtype,
+              vec_dtype, _stream(stream), flags, ctypes.byref(opts))
+    return h.value
+
+
+def spmv_plan_coo(m, n, nnz, layout, rows, cols, vals, val_dtype, vec_dtype, stream=None, flags=0, chunks=0,
+                  warps_per_cta=0, tile_items=0, stages=0):
+    h = ctypes.c_void_p()
+    opts = _lib.spmv_plan_opts(chunks, warps_per_cta, tile_items, stages)
+    _lib.call("spmv_plan_coo", ctypes.byref(h), m, n, nnz, layout, _addr(rows), _addr(cols), _addr(vals), val_dtype,
               vec_dtype, _stream(stream), flags, ctypes.byref(opts))
     return h.value
 
@@ -221,6 +230,25 @@ class Plan:
     @classmethod
     def from_matrix(cls, A, **kw):
         return cls(A.m, A.n, A.ptr, A.idx, A.vals, layout=A.layout, **kw)
+
+    @classmethod
+    def from_coo(cls, m, n, rows, cols, vals, layout="csc", vec_dtype=None, flags=0, stream=None, **opts):
+        """Plan from device triples sorted by column ("csc") or by row ("csr"); the plan builds the pointer array."""
+        import torch
+
+        self = cls.__new__(cls)
+        self.m, self.n = int(m), int(n)
+        self.layout = SPMV_CSC_WIDE if layout in ("csc", SPMV_CSC_WIDE) else SPMV_CSR_TALL
+        self.rows, self.cols, self.vals = rows, cols, vals
+        self.idx = rows if self.layout == SPMV_CSC_WIDE else cols
+        self.ptr = None
+        self.val_dtype = vals.dtype
+        self.vec_dtype = vec_dtype or (torch.float64 if vals.dtype == torch.float64 else torch.float32)
+        self.nnz = int(vals.numel())
+        self.handle = spmv_plan_coo(self.m, self.n, self.nnz, self.layout, rows, cols, vals, dtype_code(vals.dtype),
+                                    dtype_code(self.vec_dtype), stream, flags, opts.get("chunks", 0),
+                                    opts.get("warps_per_cta", 0), opts.get("tile_items", 0), opts.get("stages", 0))
+        return self
 
     def close(self):
         if getattr(self, "handle", None):

@@ -76,6 +76,8 @@ SIGNATURES = {
     "spmv_plan": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I64, _I32, _P, _P, _P, _I32, _I32, _P, _U32]),
     "spmv_plan_ex": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I64, _I32, _P, _P, _P, _I32, _I32, _P, _U32,
                             ctypes.POINTER(spmv_plan_opts)]),
+    "spmv_plan_coo": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I64, _I32, _P, _P, _P, _I32, _I32, _P, _U32,
+                             ctypes.POINTER(spmv_plan_opts)]),
     "spmv_plan_destroy": (_I32, [_P]),
     "spmv_plan_info": (_I32, [_P, ctypes.POINTER(spmv_plan_info_t)]),
     "spmv_plan_chunks": (_I32, [_P, ctypes.POINTER(spmv_chunk_t), _I32]),

@@ -282,6 +282,7 @@ void free_plan(spmv_plan_s *p) {
     if (p->hout) cudaFree(p->hout);
     if (p->hg) cudaFree(p->hg);
     if (p->ynorm) cudaFree(p->ynorm);
+    if (p->owned_ptr) cudaFree(p->owned_ptr);
     delete p;
 }
 

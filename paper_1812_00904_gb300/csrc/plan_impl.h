@@ -52,6 +52,7 @@ struct spmv_plan_s {
     std::mutex host_mu;
     void *hin = nullptr, *hout = nullptr, *hg = nullptr;
     void *ynorm = nullptr;  // A x of spmv_normal when the caller passes no buffer
+    void *owned_ptr = nullptr;  // pointer array built by spmv_plan_coo (the other arrays stay borrowed)
 
     // kernel timers (SPMV_PLAN_PROFILE)
     struct Prof {
