@@ -88,7 +88,7 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.masks = p->masks;
     sp.ntiles = p->ntiles;
     sp.mwp = p->mwp;
-    sp.stages = p->S;
+    sp.slots = p->S;
     sp.x_cap = p->x_cap;
     sp.tile_cap = p->T;
     sp.checked = (p->flags & SPMV_PLAN_NO_VALIDATE) ? 1 : 0;
@@ -134,7 +134,7 @@ void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt) {
     const int W = std::max(1, warps_for(p, mode, kbt));
     a.smemv = p->onchip;
     a.sp.vec_region_bytes = (int)vec_bytes(p, mode, kbt);
-    a.sp.stage_bytes = g.bytes;
+    a.sp.slot_bytes = g.bytes;
     a.sp.off_val = g.off_val;
     a.sp.off_mask = g.off_mask;
     a.sp.off_x = g.off_x;
@@ -388,7 +388,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     smem_max -= 1024;  // static shared memory and slack
 
-    // ---- launch configuration: tiles of T nonzeros, rounds of W tiles, S stages per CTA
+    // ---- launch configuration: tiles of T nonzeros, up to W warps per CTA, S staging slots per warp
     // default tile: 512 nonzeros (two whole 256-position steps); smaller when the matrix has
     // too few nonzeros to give every warp of a full wave about two tiles
     p->T = 512;

@@ -57,7 +57,7 @@ struct StreamParams {
     const TileMeta *meta;    // ntiles + 1 entries
     const uint32_t *masks;   // per tile: mwp words of segment-start bits
     int32_t ntiles, mwp;
-    int32_t stage_bytes, vec_region_bytes, stages, x_cap;  // per-warp slot bytes, slots per warp, window elements
+    int32_t slot_bytes, vec_region_bytes, slots, x_cap;  // per-warp slot bytes, slots per warp, window elements
     int32_t tile_cap, off_val, off_mask, off_x, off_hdr;  // slot layout: indices at 0, values, masks, windows, header
     int32_t checked;         // 1: indices not validated by the plan, checked (clamped) on every step
     int32_t kb;              // vectors in this pass (<= KB template)

@@ -30,7 +30,6 @@
 namespace gbk {
 
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;   // 2 s per pipeline wait
-constexpr int BAR_REGION_BYTES = 1024;               // the warps' slot barriers (at most 32 warps x 4 slots)
 
 __device__ __forceinline__ void copy_elem(unsigned char *d, const unsigned char *s, int es) {
     if (es == 8) {
@@ -67,11 +66,11 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
     const int W = blockDim.x >> 5;
     const int kb = (MODE == MODE_DVALUES) ? 1 : p.kb;
     const int nvec = (MODE == MODE_DVALUES) ? 1 : p.kb;
-    const int S = p.stages;
+    const int S = p.slots;
     const unsigned n_minor = static_cast<unsigned>(p.n_minor);
 
     uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
-    unsigned char *myslots = smem + p.vec_region_bytes + BAR_REGION_BYTES + (size_t)warp * S * p.stage_bytes;
+    unsigned char *myslots = smem + p.vec_region_bytes + BAR_BYTES + (size_t)warp * S * p.slot_bytes;
 
     // this CTA's tiles: the Sec. II rule over the grid; this warp's: ta + warp + k W
     const int G = gridDim.x, g = blockIdx.x;
@@ -80,25 +79,12 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
     const int tb = ta + tq + (g < tr ? 1 : 0);
     const int nk = (tb - ta > warp) ? (tb - ta - warp + W - 1) / W : 0;
 
-    // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES)
-    if constexpr (SMEMV) {
-        if constexpr (MODE == MODE_SCATTER) {
-            AT *acc = reinterpret_cast<AT *>(smem);
-            for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
-        } else {
-            XT *vs = reinterpret_cast<XT *>(smem);
-            for (int i = threadIdx.x; i < p.n_minor; i += blockDim.x) {
-#pragma unroll
-                for (int b = 0; b < KB; ++b)
-                    vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[i] : zero_of<XT>();
-            }
-        }
-    }
+    // this warp's slot barriers (used by this warp only)
     if (lane == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&myfull[s], 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    __syncwarp();
 
     // ---- tile descriptors of this warp, 32 per batch: lane j holds tile 32 * batch + j
     int4 dcur = make_int4(0, 0, 0, 0), dnxt = make_int4(0, 0, 0, 0);  // nzb, e_begin, flags, next tile's nzb
@@ -180,7 +166,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
             cnt = (c_x && nxc <= p.x_cap) ? nxc : 0;
         }
         if (ncov < 0 || ncov > p.tile_cap) cnt = 0;
-        unsigned char *dst = myslots + (size_t)s * p.stage_bytes + c_off;
+        unsigned char *dst = myslots + (size_t)s * p.slot_bytes + c_off;
         // the part below the array's last 16-byte boundary by bulk copy, the rest
         // (at most 15 bytes at the very end of an array) by plain loads
         const int end = e0 + cnt;
@@ -193,7 +179,7 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
         }
         const uint32_t total = __reduce_add_sync(FULL, bytes);
         if (lane == 0) {  // the tile's header, read by this warp when it processes the tile
-            int4 *hd = reinterpret_cast<int4 *>(myslots + (size_t)s * p.stage_bytes + p.off_hdr);
+            int4 *hd = reinterpret_cast<int4 *>(myslots + (size_t)s * p.slot_bytes + p.off_hdr);
             hd[0] = d;
             hd[1] = make_int4(e1, xbase, nxc, 0);
         }
@@ -203,12 +189,28 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
         if (bytes) bulk_g2s(dst, c_src + (size_t)e0 * c_es, bytes, &myfull[s]);
     };
 
-    for (int k = 0; k < min(S, nk); ++k) issue(k, k);
+    for (int k = 0; k < min(S, nk); ++k) issue(k, k);  // the first copies fly while the vector is staged
+
+    // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES)
+    if constexpr (SMEMV) {
+        if constexpr (MODE == MODE_SCATTER) {
+            AT *acc = reinterpret_cast<AT *>(smem);
+            for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
+        } else {
+            XT *vs = reinterpret_cast<XT *>(smem);
+            for (int i = threadIdx.x; i < p.n_minor; i += blockDim.x) {
+#pragma unroll
+                for (int b = 0; b < KB; ++b)
+                    vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[i] : zero_of<XT>();
+            }
+        }
+    }
+    __syncthreads();
 
     int s = 0;        // slot of tile k
     uint32_t ph = 0;  // phase parity of that slot's barrier
     for (int k = 0; k < nk; ++k) {
-        unsigned char *slot = myslots + (size_t)s * p.stage_bytes;
+        unsigned char *slot = myslots + (size_t)s * p.slot_bytes;
         bool ok = mbar_wait_bounded(&myfull[s], ph, WAIT_LIMIT_NS);
         ok = __all_sync(FULL, ok);
         if (!ok) {
