@@ -403,7 +403,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
-    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 24]");
+    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 16]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
     p->x_cap = (int)align_up((size_t)p->T / 4 + 16, 8);  // columns of a tile's window (fall back to global beyond)
     p->smem_max = smem_max;

@@ -15,8 +15,8 @@ enum Mode : int {
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
-constexpr int MAX_WARPS = 24;    // warps per CTA of the single-vector passes
-constexpr int MAX_WARPS_KB = 16; // warps per CTA of the multi-vector passes (more registers per thread)
+constexpr int MAX_WARPS = 16;    // warps per CTA of the single-vector passes (room for 128 registers a thread)
+constexpr int MAX_WARPS_KB = 16; // warps per CTA of the multi-vector passes
 constexpr int MAX_STAGES = 4;    // slots per warp
 constexpr int BAR_BYTES = 1024;  // slot barriers at the start of the staging area
 
