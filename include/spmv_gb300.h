@@ -84,8 +84,9 @@ typedef struct spmv_plan_s *spmv_plan_t;
 /* Optional tuning of a plan; zero fields take the defaults. */
 typedef struct {
     int32_t chunks;        /* P, the number of reporting chunks (Sec. II); 0 = min(tiles, 16 per SM) */
-    int32_t warps_per_cta; /* most warps per CTA, 1..16; 0 = 16; every pass runs as many as its
-                              staging slots fit in shared memory */
+    int32_t warps_per_cta; /* most warps per CTA, 1..24 (at most 16 run the multi-vector passes);
+                              0 = 24; every pass runs as many as its staging slots fit in shared
+                              memory (up to 16 warps with 128 registers a thread, more with 80) */
     int32_t tile_items;    /* nonzeros per execution tile, a multiple of 8 in [8, 992]; 0 = 512, or
                               down to 64 when nnz < 32 x 512 per SM (about two tiles per warp) */
     int32_t stages;        /* staging slots per warp (tiles in flight + 1), 2..4; 0 = 2 */

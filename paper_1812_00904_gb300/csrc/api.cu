@@ -125,7 +125,9 @@ int warps_for(const spmv_plan_s *p, int mode, int kbt) {
     const SlotGeom g = slot_geom(p, mode, kbt);
     const size_t room = (size_t)p->smem_max > vec + BAR_BYTES ? (size_t)p->smem_max - vec - BAR_BYTES : 0;
     const int fit = (int)std::min<size_t>(room / ((size_t)p->S * g.bytes), 64);
-    return std::min({p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
+    const int w = std::min({p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
+    // one warp beyond WARPS_REGS costs the others their larger register budget: not worth it
+    return w == WARPS_REGS + 1 ? WARPS_REGS : w;
 }
 
 // Launch geometry of one streaming pass.
@@ -403,7 +405,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     if (p->T < 8 || p->T > 992 || (p->T % 8) != 0)
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
-    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 16]");
+    if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 24]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
     p->x_cap = (int)align_up((size_t)p->T / 4 + 16, 8);  // columns of a tile's window (fall back to global beyond)
     p->smem_max = smem_max;

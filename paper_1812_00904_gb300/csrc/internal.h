@@ -15,8 +15,9 @@ enum Mode : int {
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
-constexpr int MAX_WARPS = 16;    // warps per CTA of the single-vector passes (room for 128 registers a thread)
+constexpr int MAX_WARPS = 24;    // warps per CTA of the single-vector passes (80 registers a thread beyond 16)
 constexpr int MAX_WARPS_KB = 16; // warps per CTA of the multi-vector passes
+constexpr int WARPS_REGS = 16;   // warps per CTA up to which a kernel may use 128 registers a thread
 constexpr int MAX_STAGES = 4;    // slots per warp
 constexpr int BAR_BYTES = 1024;  // slot barriers at the start of the staging area
 

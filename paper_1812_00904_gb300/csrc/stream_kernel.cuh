@@ -57,8 +57,9 @@ struct RtBool {  // a flag known only at run time, passed where a BoolC may be
     bool value;
 };
 
-template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
-__global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
+// WB: the most warps a launch of this instantiation may have (its register budget).
+template <typename VT, typename XT, int MODE, int KB, bool SMEMV, int WB>
+__global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
     using AT = typename Acc<VT>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
@@ -701,10 +702,12 @@ __global__ void __launch_bounds__((KB == 1 ? MAX_WARPS : MAX_WARPS_KB) * 32, 1) 
     }
 }
 
-// Host-side launch of one instantiation; sets the shared-memory limit once.
-template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
-cudaError_t launch_one(const LaunchArgs &a) {
-    auto kern = stream_kernel<VT, XT, MODE, KB, SMEMV>;
+// Host-side launch of one instantiation; sets the shared-memory limit once per kernel.
+// Up to WARPS_REGS warps run a kernel compiled for 128 registers a thread; more warps
+// (single-vector passes only) run one compiled for 80.
+template <typename VT, typename XT, int MODE, int KB, bool SMEMV, int WB>
+cudaError_t launch_wb(const LaunchArgs &a) {
+    auto kern = stream_kernel<VT, XT, MODE, KB, SMEMV, WB>;
     static int configured = 0;
     if (configured < a.smem) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
@@ -713,6 +716,14 @@ cudaError_t launch_one(const LaunchArgs &a) {
     }
     kern<<<a.grid, a.block, a.smem, a.stream>>>(a.sp);
     return cudaGetLastError();
+}
+
+template <typename VT, typename XT, int MODE, int KB, bool SMEMV>
+cudaError_t launch_one(const LaunchArgs &a) {
+    if constexpr (KB == 1) {
+        if (a.block > WARPS_REGS * 32) return launch_wb<VT, XT, MODE, KB, SMEMV, MAX_WARPS>(a);
+    }
+    return launch_wb<VT, XT, MODE, KB, SMEMV, WARPS_REGS>(a);
 }
 
 }  // namespace gbk

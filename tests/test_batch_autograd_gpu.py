@@ -43,8 +43,8 @@ def test_batch_on_a_wide_round_plan(layout):
     of warps over the same tiles: the sums must agree bit for bit."""
     m, n = (900, 40_000) if layout == "csc" else (40_000, 900)
     A = synth.random_matrix(m, n, layout, density=0.004, seed=77)
-    plan, stored = make_plan(A, torch.float32, tile_items=256, stages=2, warps_per_cta=16)
-    assert plan.info()["warps_per_cta"] == 16
+    plan, stored = make_plan(A, torch.float32, tile_items=256, stages=2, warps_per_cta=24)
+    assert plan.info()["warps_per_cta"] == 24
     k = 5
     X = torch.stack([dev_vec(synth.uniform_vector(n, 100 + b), torch.float32) for b in range(k)])
     V = torch.stack([dev_vec(synth.uniform_vector(m, 200 + b), torch.float32) for b in range(k)])

@@ -116,7 +116,7 @@ def test_setup_and_products_match_oracle(case, P):
     check_products(plan, stored, synth.uniform_vector(A.n, 1), synth.uniform_vector(A.m, 2), 1e-5, f"{case} P={P}")
 
 
-@pytest.mark.parametrize("tile_items,stages,warps", [(64, 2, 1), (128, 4, 3), (992, 2, 4), (256, 3, 16), (40, 4, 7), (256, 2, 16), (384, 2, 12), (512, 2, 16)])
+@pytest.mark.parametrize("tile_items,stages,warps", [(64, 2, 1), (128, 4, 3), (992, 2, 4), (256, 3, 16), (40, 4, 7), (256, 2, 24), (384, 2, 20), (256, 2, 16), (512, 2, 16)])
 def test_tiling_options(tile_items, stages, warps):
     A = synth.random_matrix(700, 30_000, "csc", degrees=np.minimum(np.random.default_rng(1).zipf(1.9, 30_000), 700),
                             seed=9)
