@@ -51,7 +51,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_name: str, workload: str):
+def ncu_traffic(kernel_name: str, workload: str, order: str):
     """DRAM bytes per launch from the committed ncu summary, if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
@@ -60,7 +60,8 @@ def ncu_traffic(kernel_name: str, workload: str):
     except Exception:
         return None
     e = d.get(kernel_name)
-    if not e or e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload:
+    if (not e or e.get("source_hash") != kernel_source_hash() or e.get("workload") != workload
+            or e.get("nonzero_order", "stored") != order):
         return None
     return e.get("bytes_per_launch")
 
@@ -432,7 +433,8 @@ def run_ours(args):
 
     A = synth.wide_fp32_large(1, device=dev, scale=args.scale)  # every rank holds its own replica
     m, n, nnz = A.m, A.n, A.nnz
-    plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=pkg.SPMV_PLAN_PROFILE, warps_per_cta=args.warps,
+    order = 0 if args.stored_order else pkg.SPMV_PLAN_BANK_ORDER
+    plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order, warps_per_cta=args.warps,
                     tile_items=args.tile_items, stages=args.stages)
     info = plan.info()
     g = torch.Generator(device=dev)
@@ -472,6 +474,20 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     clocks = sampler.stop(t0, t1)
     plan.check()
+    # kernel durations: the same K steps again with every launch bracketed by CUDA events on
+    # the launching stream (the events make each kernel drain before the next one starts, so
+    # the whole-step number above is taken without them)
+    pkg.spmv_profile_enable(plan.handle, True)
+    ev2 = torch.cuda.Event(enable_timing=True)
+    ev3 = torch.cuda.Event(enable_timing=True)
+    ev2.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev3.record(stream)
+    torch.cuda.synchronize()
+    pkg.spmv_profile_enable(plan.handle, False)
+    plan.check()
+    ms_profiled = ev2.elapsed_time(ev3)
     kt = {k: pkg.spmv_profile_read(plan.handle, k) for k in range(5)}
     ms_max = max_over_ranks(ms, world, dev)
     b_spmv, b_spvtm = pair_bytes(m, n, nnz)
@@ -488,8 +504,11 @@ def run_ours(args):
     achieved = kbytes / avg_s / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": ncu_traffic(dom, WORKLOAD) if args.scale == 1.0 else None, "bytes_per_launch": kbytes,
-            "avg_launch_us": round(avg_s * 1e6, 2)}
+            "traffic": ncu_traffic(dom, WORKLOAD, "stored" if args.stored_order else "bank")
+            if args.scale == 1.0 else None, "bytes_per_launch": kbytes,
+            "avg_launch_us": round(avg_s * 1e6, 2),
+            "timing": f"per-kernel CUDA events over a second pass of the {args.steps} steps "
+                      f"({ms_profiled / args.steps:.4f} ms per step with the events)"}
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -530,8 +549,13 @@ def run_ours(args):
         tc = time.perf_counter() - tc0
         extras["cgls"] = {"iterations": it, "ms_per_iteration": round(tc * 1e3 / max(it, 1), 4),
                           "rel_grad": rel, "note": "wall clock of the call, including its setup"}
+        # the same matrix multiplied in the caller's stored order (no plan-owned copy)
+        if order:
+            ps = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc")
+            extras["stored_order"] = time_pair_gbs(pkg, ps, m, n, nnz, "csc", max(20, args.steps // 5))
+            ps.close()
         vb = A.vals.to(torch.bfloat16)
-        pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32)
+        pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32, flags=order)
         extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),
                                      workload=WORKLOAD.replace("fp32", "bf16values"))
         pb.close()
@@ -550,7 +574,9 @@ def run_ours(args):
                           "step": "one SpMV + one SpVTM (Sec. V wrap)", "l2": "inputs larger than L2 (no flush)",
                           "parallelism": f"replicas x{world}", "chunks": info["chunks"], "ctas": info["ctas"],
                           "warps_per_cta": info["warps_per_cta"], "tile_items": info["tile_items"],
-                          "stages": info["stages"], "zones": info["zones"]},
+                          "stages": info["stages"], "zones": info["zones"],
+                          "nonzero_order": "stored" if args.stored_order else
+                          "bank order (plan-owned copy, permuted within each column)"},
                "gflops": round(2 * 2 * nnz * args.steps * world / (ms_max / 1e3) / 1e9, 1),
                "frac_of_hbm_peak": round(value / world / peak, 4),
                "ops": {"spmv_gbs": round(b_spmv / (spmv_ms / 1e3) / 1e9, 1),
@@ -566,7 +592,7 @@ def run_ours(args):
         del A, x, v, y, u
         torch.cuda.empty_cache()
         T = synth.tall_fp32_large(2, device=dev)
-        pt = pkg.Plan(T.m, T.n, T.ptr, T.idx, T.vals, layout="csr")
+        pt = pkg.Plan(T.m, T.n, T.ptr, T.idx, T.vals, layout="csr", flags=order)
         extras["tall_csr"] = dict(time_pair_gbs(pkg, pt, T.m, T.n, T.nnz, "csr", max(20, args.steps // 5)),
                                   workload=f"tall_csr_m{T.m}_n{T.n}_fp32_powerlaw2.2_20dense", nnz=T.nnz)
         pt.close()
@@ -598,6 +624,8 @@ def main(argv=None):
     ap.add_argument("--warps", type=int, default=0, help="warps (chunks) per CTA; 0 = library default")
     ap.add_argument("--tile-items", type=int, default=0, help="merge items per staged tile; 0 = library default")
     ap.add_argument("--stages", type=int, default=0, help="staging buffers per warp; 0 = library default")
+    ap.add_argument("--stored-order", action="store_true",
+                    help="multiply in the stored nonzero order (no bank-ordered plan copy)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -80,6 +80,13 @@ typedef struct spmv_plan_s *spmv_plan_t;
                                        spmv_check).  A validated plan relies on idx staying unchanged. */
 #define SPMV_PLAN_PROFILE 0x2u      /* time every kernel launch with CUDA events (spmv_profile_read) */
 #define SPMV_PLAN_SHORT_IN_GLOBAL 0x4u /* keep the short vector in global memory even when it fits on chip */
+#define SPMV_PLAN_BANK_ORDER 0x8u   /* keep a plan-owned copy of idx and vals in which the nonzeros of every
+                                       column (row for CSR) are permuted so that the short-vector entries one
+                                       warp instruction touches fall into distinct shared-memory banks.  Costs
+                                       nnz x (4 + value size) bytes for the plan's life and as much again for
+                                       scratch during spmv_plan; idx and vals are not read after spmv_plan
+                                       returns; results equal the stored order's up to the order of rounding;
+                                       spmv_dvalues answers SPMV_ERR_UNSUPPORTED (its g would be permuted). */
 
 /* Optional tuning of a plan; zero fields take the defaults. */
 typedef struct {
@@ -201,16 +208,31 @@ spmv_status spmv_batch(spmv_plan_t plan, int32_t op, int32_t k, const void *in, 
  */
 spmv_status spmv_dvalues(spmv_plan_t plan, const void *r, const void *x, void *g, void *stream);
 
+/*
+ * spmv_plan_export -- copy the nonzeros the plan multiplies by into caller buffers:
+ * idx_out (nnz int32) and vals_out (nnz values of val_dtype), device or host
+ * pointers, in the plan's storage order (the caller's order, or the plan's bank
+ * order under SPMV_PLAN_BANK_ORDER).  Synchronizes `stream`.
+ * Errors: SPMV_ERR_INVALID_ARG (null plan or buffer), SPMV_ERR_CUDA.
+ */
+spmv_status spmv_plan_export(spmv_plan_t plan, int32_t *idx_out, void *vals_out, void *stream);
+
 /* Synchronize `stream`, then read and clear the plan's device error word.
  * Returns SPMV_ERR_DEVICE (with a message) if any kernel flagged a failure. */
 spmv_status spmv_check(spmv_plan_t plan, void *stream);
 
-/* Kernel timers of a plan created with SPMV_PLAN_PROFILE.  kernel: 0 = chunk
- * scatter (SpMV local), 1 = partial combine, 2 = chunk dot (SpVTM local),
- * 3 = zone fixup, 4 = dvalues.  Synchronizes the device.  *ms = summed event
- * time, *launches = number of timed launches. */
+/* Kernel timers of a plan created with SPMV_PLAN_PROFILE (or switched on with
+ * spmv_profile_enable).  kernel: 0 = chunk scatter (SpMV local), 1 = partial
+ * combine, 2 = chunk dot (SpVTM local), 3 = zone fixup, 4 = dvalues.
+ * Synchronizes the device.  *ms = summed event time, *launches = number of
+ * timed launches.  Timing brackets every launch with two events, which waits
+ * for each kernel to drain before the next starts: a profiled sequence of
+ * launches runs a little slower than an unprofiled one. */
 spmv_status spmv_profile_read(spmv_plan_t plan, int32_t kernel, double *ms, int64_t *launches);
 spmv_status spmv_profile_reset(spmv_plan_t plan);
+/* Switch the kernel timers of a plan on (on != 0) or off for the launches that follow;
+ * the sums read by spmv_profile_read are kept.  Errors: SPMV_ERR_INVALID_ARG. */
+spmv_status spmv_profile_enable(spmv_plan_t plan, int32_t on);
 
 /*
  * spmv_noalloc -- y = A x for a wide CSC matrix (FP32 values and vectors)

@@ -12,15 +12,16 @@ import ctypes
 
 from . import _lib
 from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, SPMV_F64, SPMV_OP_AX, SPMV_OP_VTA,
-                   SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL, SpmvError)
+                   SPMV_PLAN_BANK_ORDER, SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL,
+                   SpmvError)
 
 __all__ = [
     "spmv_plan", "spmv_plan_ex", "spmv_plan_coo", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
-    "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_normal", "spmv_cgls", "spmv_check", "spmv_profile_read", "spmv_profile_reset", "spmv_last_error",
+    "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_normal", "spmv_cgls", "spmv_check", "spmv_plan_export", "spmv_profile_read", "spmv_profile_reset", "spmv_profile_enable", "spmv_last_error",
     "spmv_version", "serve_create", "serve_register", "serve_register_host", "serve_submit", "serve_poll",
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
     "SPMV_CSC_WIDE", "SPMV_CSR_TALL", "SPMV_F64", "SPMV_F32", "SPMV_BF16", "SPMV_F16", "SPMV_OP_AX", "SPMV_OP_VTA",
-    "SPMV_PLAN_NO_VALIDATE", "SPMV_PLAN_PROFILE", "SPMV_PLAN_SHORT_IN_GLOBAL",
+    "SPMV_PLAN_NO_VALIDATE", "SPMV_PLAN_PROFILE", "SPMV_PLAN_SHORT_IN_GLOBAL", "SPMV_PLAN_BANK_ORDER",
 ]
 
 
@@ -119,6 +120,14 @@ def spmv_dvalues(plan, r, x, g, stream=None):
 
 def spmv_check(plan, stream=None):
     _lib.call("spmv_check", plan, _stream(stream))
+
+
+def spmv_plan_export(plan, idx_out, vals_out, stream=None):
+    _lib.call("spmv_plan_export", plan, _addr(idx_out), _addr(vals_out), _stream(stream))
+
+
+def spmv_profile_enable(plan, on):
+    _lib.call("spmv_profile_enable", plan, 1 if on else 0)
 
 
 def spmv_profile_read(plan, kernel: int):
@@ -313,6 +322,16 @@ class Plan:
 
     def check(self, stream=None):
         spmv_check(self.handle, stream)
+
+    def export(self, stream=None):
+        """(idx, vals): device copies of the nonzeros in the plan's storage order."""
+        import torch
+
+        dev = self.vals.device
+        idx = torch.empty(self.nnz, dtype=torch.int32, device=dev)
+        vals = torch.empty(self.nnz, dtype=self.val_dtype, device=dev)
+        spmv_plan_export(self.handle, idx, vals, stream)
+        return idx, vals
 
     def profile(self, kernel: int):
         return spmv_profile_read(self.handle, kernel)

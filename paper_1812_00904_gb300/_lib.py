@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_ARG", 2: "SPMV_ERR_BAD_MATRIX
 SPMV_CSC_WIDE, SPMV_CSR_TALL = 0, 1
 SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_F16 = 0, 1, 2, 3
 SPMV_OP_AX, SPMV_OP_VTA = 0, 1
-SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL = 0x1, 0x2, 0x4
+SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL, SPMV_PLAN_BANK_ORDER = 0x1, 0x2, 0x4, 0x8
 
 KERNEL_SCATTER, KERNEL_COMBINE, KERNEL_SEGDOT, KERNEL_FIXUP, KERNEL_DVALUES = 0, 1, 2, 3, 4
 
@@ -86,6 +86,8 @@ SIGNATURES = {
     "spmv_batch": (_I32, [_P, _I32, _I32, _P, _I64, _P, _I64, _P]),
     "spmv_dvalues": (_I32, [_P, _P, _P, _P, _P]),
     "spmv_check": (_I32, [_P, _P]),
+    "spmv_plan_export": (_I32, [_P, _P, _P, _P]),
+    "spmv_profile_enable": (_I32, [_P, _I32]),
     "spmv_profile_read": (_I32, [_P, _I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "spmv_profile_reset": (_I32, [_P]),
     "spmv_noalloc": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P]),

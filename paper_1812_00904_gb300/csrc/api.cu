@@ -60,7 +60,7 @@ struct ProfScope {
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
     ProfScope(spmv_plan_s *p_, int k, cudaStream_t s_) : p(p_), kernel(k), s(s_) {
-        if (p->flags & SPMV_PLAN_PROFILE) {
+        if (p->prof_on.load(std::memory_order_relaxed)) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, s);
@@ -170,7 +170,7 @@ spmv_status set_error(spmv_status st, const std::string &msg) {
 }
 
 size_t plan_footprint(const spmv_plan_s *p) {
-    return p->ws_bytes + (size_t)p->nnz * (4 + p->sv) + (size_t)(p->n_major + 1) * 4;
+    return p->ws_bytes + p->owned_bytes + (size_t)p->nnz * (4 + p->sv) + (size_t)(p->n_major + 1) * 4;
 }
 
 spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
@@ -285,6 +285,7 @@ void free_plan(spmv_plan_s *p) {
     if (p->hg) cudaFree(p->hg);
     if (p->ynorm) cudaFree(p->ynorm);
     if (p->owned_ptr) cudaFree(p->owned_ptr);
+    if (p->owned_nz) cudaFree(p->owned_nz);
     delete p;
 }
 
@@ -376,6 +377,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->val_t = val_dtype;
     p->vec_t = vec_dtype;
     p->flags = flags;
+    p->prof_on = (flags & SPMV_PLAN_PROFILE) != 0;
     p->n_major = (int)(layout == SPMV_CSC_WIDE ? n : m);
     p->n_minor = (int)(layout == SPMV_CSC_WIDE ? m : n);
     p->ptr = ptr;
@@ -481,6 +483,26 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         }
     }
 
+    // ---- the plan's own copy of the nonzeros in bank order (same nonzeros, permuted within
+    // each segment); the caller's idx/vals are not read after this point
+    if ((flags & SPMV_PLAN_BANK_ORDER) && nnz > 0) {
+        const size_t ib = align_up((size_t)nnz * 4, 256);
+        const size_t vb = align_up((size_t)nnz * p->sv, 256);
+        CUDA_TRY(cudaMalloc(&p->owned_nz, ib + vb));
+        p->owned_bytes = ib + vb;
+        int32_t *slots = nullptr;
+        CUDA_TRY(cudaMalloc(&slots, (size_t)nnz * 4));
+        int32_t *oidx = static_cast<int32_t *>(p->owned_nz);
+        void *ovals = static_cast<char *>(p->owned_nz) + ib;
+        cudaError_t ce = launch_bank_order(ptr, p->n_major, (int)nnz, idx, vals, p->sv, oidx, ovals, slots, p->T,
+                                           p->sx == 8 ? 16 : 32, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        cudaFree(slots);
+        if (ce != cudaSuccess) return set_error(SPMV_ERR_CUDA, std::string("bank order: ") + cudaGetErrorString(ce));
+        p->idx = oidx;
+        p->vals = ovals;
+    }
+
     // ---- Sec. II partition and Sec. IV-B set-up on the device: reporting chunks
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
@@ -579,7 +601,7 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->max_chunk_nnz = p->max_chunk;
     info->min_chunk_nnz = p->min_chunk;
     info->imbalance = p->nnz > 0 ? (double)p->P * (double)(p->max_chunk - p->min_chunk) / (double)p->nnz : 0.0;
-    info->workspace_bytes = (int64_t)p->ws_bytes;
+    info->workspace_bytes = (int64_t)(p->ws_bytes + p->owned_bytes);
     info->setup_ms = p->setup_ms;
     return SPMV_OK;
 }
@@ -646,6 +668,8 @@ spmv_status spmv_batch(spmv_plan_t p, int32_t op, int32_t k, const void *in, int
 spmv_status spmv_dvalues(spmv_plan_t p, const void *r, const void *x, void *g, void *stream) {
     if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
     if (!r || !x || (!g && p->nnz > 0)) return set_error(SPMV_ERR_INVALID_ARG, "null pointer");
+    if (p->owned_nz)
+        return set_error(SPMV_ERR_UNSUPPORTED, "spmv_dvalues on a bank-ordered plan (its values are permuted)");
     if (p->nnz == 0) return SPMV_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const PtrKind kr = classify(r), kx = classify(x), kg = classify(g);
@@ -673,6 +697,17 @@ spmv_status spmv_dvalues(spmv_plan_t p, const void *r, const void *x, void *g, v
     spmv_status st = run_dvalues(p, dr, dx, dg, s);
     if (st != SPMV_OK) return st;
     if (kg == PK_HOST) CUDA_TRY(cudaMemcpyAsync(g, dg, (size_t)p->nnz * p->sv, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+spmv_status spmv_plan_export(spmv_plan_t p, int32_t *idx_out, void *vals_out, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    if (p->nnz == 0) return SPMV_OK;
+    if (!idx_out || !vals_out) return set_error(SPMV_ERR_INVALID_ARG, "null pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemcpyAsync(idx_out, p->idx, (size_t)p->nnz * 4, cudaMemcpyDefault, s));
+    CUDA_TRY(cudaMemcpyAsync(vals_out, p->vals, (size_t)p->nnz * p->sv, cudaMemcpyDefault, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SPMV_OK;
 }
@@ -710,6 +745,12 @@ spmv_status spmv_profile_read(spmv_plan_t p, int32_t kernel, double *ms, int64_t
     p->prof.clear();
     if (ms) *ms = p->prof_ms[kernel];
     if (launches) *launches = p->prof_n[kernel];
+    return SPMV_OK;
+}
+
+spmv_status spmv_profile_enable(spmv_plan_t p, int32_t on) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    p->prof_on.store(on != 0);
     return SPMV_OK;
 }
 

@@ -324,4 +324,94 @@ cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles,
     return cudaGetLastError();
 }
 
+// Plan-owned copy of the nonzeros, permuted within every major segment (a column of a
+// CSC matrix, a row of a CSR one), so that the minor indices one warp instruction of the
+// streaming kernels reads or updates in shared memory fall into distinct banks.  The
+// streaming kernels touch tile positions r (r = nonzero position mod T) in two patterns:
+// the scatter pass 32 consecutive ones (r = 32a + b, b = 0..31), the segmented pass one of
+// 8 positions per lane, 8l + (e ^ 4((l >> 2) & 1)).  A position r asks for bank
+// ((r & 31) + ((r >> 5) & 7)) mod NB, which is one-to-one over the lanes in both patterns
+// (NB = 32 banks of 4-byte words; 16 for 8-byte elements).  One thread per segment: its
+// nonzeros are pooled by bank; every position, in order, takes a nonzero of the bank it
+// asks for while that pool lasts, else one of the fullest pool.  Within a bank the stored
+// order is kept.  Each thread reads and writes only its clamped range [s, e), so a
+// malformed ptr (an unvalidated plan) stays in bounds.
+template <typename W>
+__global__ void bank_order_kernel(const int32_t *__restrict__ ptr, int n_major, int nnz,
+                                  const int32_t *__restrict__ idx, const W *__restrict__ vals,
+                                  int32_t *__restrict__ oidx, W *__restrict__ ovals, int32_t *__restrict__ slots,
+                                  int T, int nbm) {
+    const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (c >= n_major) return;
+    const int s = min(max(ptr[c], 0), nnz);
+    const int e = min(max(ptr[c + 1], s), nnz);
+    if (e - s <= 1) {
+        if (e > s) {
+            oidx[s] = idx[s];
+            ovals[s] = vals[s];
+        }
+        return;
+    }
+    int cnt[32], off[32], used[32];
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        cnt[b] = 0;
+        used[b] = 0;
+    }
+    for (int j = s; j < e; ++j) ++cnt[idx[j] & nbm];
+    int o = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        off[b] = o;
+        o += cnt[b];
+    }
+    // the bank of every position; the positions given to bank b are listed in order at
+    // slots[s + off[b] ..]
+    int r = s % T;
+    for (int q = s; q < e; ++q) {
+        int b = ((r & 31) + ((r >> 5) & 7)) & nbm;
+        if (used[b] == cnt[b]) {
+            int left = -1;
+            for (int k = 0; k <= nbm; ++k) {
+                if (cnt[k] - used[k] > left) {
+                    left = cnt[k] - used[k];
+                    b = k;
+                }
+            }
+        }
+        slots[s + off[b] + used[b]] = q;
+        ++used[b];
+        if (++r == T) r = 0;
+    }
+#pragma unroll
+    for (int b = 0; b < 32; ++b) used[b] = 0;
+    for (int j = s; j < e; ++j) {
+        const int b = idx[j] & nbm;
+        const int q = slots[s + off[b] + used[b]];
+        ++used[b];
+        if (q >= s && q < e) {
+            oidx[q] = idx[j];
+            ovals[q] = vals[j];
+        }
+    }
+}
+
+cudaError_t launch_bank_order(const int32_t *ptr, int n_major, int nnz, const int32_t *idx, const void *vals,
+                              int val_bytes, int32_t *oidx, void *ovals, int32_t *slots, int T, int banks,
+                              cudaStream_t s) {
+    if (n_major <= 0 || nnz <= 0) return cudaSuccess;
+    const int grid = (n_major + 127) / 128;
+    const int nbm = banks - 1;
+    if (val_bytes == 8)
+        bank_order_kernel<uint64_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint64_t *>(vals),
+                                                         oidx, static_cast<uint64_t *>(ovals), slots, T, nbm);
+    else if (val_bytes == 4)
+        bank_order_kernel<uint32_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint32_t *>(vals),
+                                                         oidx, static_cast<uint32_t *>(ovals), slots, T, nbm);
+    else
+        bank_order_kernel<uint16_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint16_t *>(vals),
+                                                         oidx, static_cast<uint16_t *>(ovals), slots, T, nbm);
+    return cudaGetLastError();
+}
+
 }  // namespace gbk

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -53,12 +54,15 @@ struct spmv_plan_s {
     void *hin = nullptr, *hout = nullptr, *hg = nullptr;
     void *ynorm = nullptr;  // A x of spmv_normal when the caller passes no buffer
     void *owned_ptr = nullptr;  // pointer array built by spmv_plan_coo (the other arrays stay borrowed)
+    void *owned_nz = nullptr;   // idx and vals in bank order (SPMV_PLAN_BANK_ORDER)
+    size_t owned_bytes = 0;
 
     // kernel timers (SPMV_PLAN_PROFILE)
     struct Prof {
         int kernel;
         cudaEvent_t a, b;
     };
+    std::atomic<bool> prof_on{false};  // SPMV_PLAN_PROFILE at creation; spmv_profile_enable later
     std::mutex prof_mu;
     std::vector<Prof> prof;
     double prof_ms[5] = {0, 0, 0, 0, 0};
@@ -74,6 +78,11 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
 // op product on device vectors, any k (split into passes of batch_width)
 spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *const *out, cudaStream_t s);
 size_t plan_footprint(const spmv_plan_s *p);
+// Plan-owned copy of idx/vals, permuted within each segment so that one warp instruction of the
+// streaming kernels meets distinct shared-memory banks (banks: 32, or 16 for 8-byte vectors).
+cudaError_t launch_bank_order(const int32_t *ptr, int n_major, int nnz, const int32_t *idx, const void *vals,
+                              int val_bytes, int32_t *oidx, void *ovals, int32_t *slots, int T, int banks,
+                              cudaStream_t s);
 spmv_status set_error(spmv_status st, const std::string &msg);
 
 }  // namespace gbk

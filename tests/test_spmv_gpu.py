@@ -289,3 +289,31 @@ def test_stale_slot_contents_do_not_leak(layout):
         assert_close(y, oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, "y after a poisoned launch")
         assert_close(u, oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, "u after a poisoned launch")
     good.check()
+
+
+def test_kernel_timers_count_launches_and_switch_on_and_off():
+    A = synth.random_matrix(200, 30_000, "csc", density=0.01, seed=7)
+    plan, _ = make_plan(A, torch.float32, flags=pkg.SPMV_PLAN_PROFILE)
+    x = dev_vec(synth.uniform_vector(A.n, 1), torch.float32)
+    v = dev_vec(synth.uniform_vector(A.m, 2), torch.float32)
+    plan.spmv(x)
+    plan.spvtm(v)
+    ms, n = pkg.spmv_profile_read(plan.handle, 0)  # chunk scatter
+    assert n == 1 and ms > 0
+    assert pkg.spmv_profile_read(plan.handle, 2)[1] == 1  # chunk dot
+    pkg.spmv_profile_enable(plan.handle, False)
+    plan.spmv(x)
+    assert pkg.spmv_profile_read(plan.handle, 0)[1] == 1
+    pkg.spmv_profile_enable(plan.handle, True)
+    plan.spmv(x)
+    assert pkg.spmv_profile_read(plan.handle, 0)[1] == 2
+    pkg.spmv_profile_reset(plan.handle)
+    assert pkg.spmv_profile_read(plan.handle, 0) == (0.0, 0)
+    quiet, _ = make_plan(A, torch.float32)
+    quiet.spmv(x)
+    assert pkg.spmv_profile_read(quiet.handle, 0)[1] == 0
+    pkg.spmv_profile_enable(quiet.handle, True)
+    quiet.spmv(x)
+    assert pkg.spmv_profile_read(quiet.handle, 0)[1] == 1
+    plan.check()
+    quiet.check()
