@@ -294,6 +294,44 @@ def small_fp64_flushed(pkg, dev, reps: int = 50):
     return res
 
 
+def ops_alone(pkg, plan, m, n, nnz, reps: int = 15, per: int = 20):
+    """Each product timed alone: `reps` batches of `per` back-to-back calls of one op (CUDA events
+    per batch on the launching stream); median and min over the batches of the mean call time."""
+    import statistics
+
+    import torch
+
+    dev = plan.vals.device
+    g = torch.Generator(device=dev)
+    g.manual_seed(13)
+    x = torch.rand(n, generator=g, device=dev) * 2 - 1
+    v = torch.rand(m, generator=g, device=dev) * 2 - 1
+    y = torch.empty(m, device=dev)
+    u = torch.empty(n, device=dev)
+    stream = torch.cuda.current_stream()
+    b_spmv, b_spvtm = pair_bytes(m, n, nnz)
+    out = {}
+    for name, call, b in (("spmv", lambda: pkg.spmv(plan.handle, x, y, stream), b_spmv),
+                          ("spvtm", lambda: pkg.spvtm(plan.handle, v, u, stream), b_spvtm)):
+        for _ in range(3):
+            call()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(per):
+                call()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / per)
+        med, mn = statistics.median(times), min(times)
+        out[name] = {"ms_median": round(med, 4), "ms_min": round(mn, 4), "gbs_median": round(b / med / 1e6, 1),
+                     "gbs_best": round(b / mn / 1e6, 1), "calls": reps * per}
+    plan.check()
+    return out
+
+
 def batched_rate(pkg, plan, m, n, nnz, k, steps):
     """Vectors/s and effective GB/s of k-vector SpMV and SpVTM passes (matrix streamed once per pass)."""
     import torch
@@ -538,6 +576,7 @@ def run_ours(args):
     extras = None
     if rank == 0 and world == 1 and not args.skip_extras:
         extras = {}
+        extras["ops_alone"] = ops_alone(pkg, plan, m, n, nnz)
         extras["batched_k8"] = batched_rate(pkg, plan, m, n, nnz, 8, max(10, args.steps // 20))
         extras["wide_fp64_small"] = small_fp64_flushed(pkg, dev)
         # least squares by CGLS on the same matrix: one SpMV + one SpVTM + vector updates per iteration

@@ -87,6 +87,12 @@ typedef struct spmv_plan_s *spmv_plan_t;
                                        scratch during spmv_plan; idx and vals are not read after spmv_plan
                                        returns; results equal the stored order's up to the order of rounding;
                                        spmv_dvalues answers SPMV_ERR_UNSUPPORTED (its g would be permuted). */
+#define SPMV_PLAN_COO_UNSORTED 0x10u /* spmv_plan_coo only: the triples may come in any order; the plan sorts
+                                       them on the device by (major, minor) index, stably (duplicates keep
+                                       their input order), into its own copy of the minor indices and values
+                                       (nnz x (4 + value size) bytes; about 3 x nnz x 12 bytes of scratch
+                                       during the call).  Both indices are range-checked even with
+                                       SPMV_PLAN_NO_VALIDATE. */
 
 /* Optional tuning of a plan; zero fields take the defaults. */
 typedef struct {
@@ -155,8 +161,12 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
  *   rows, cols (nnz int32 each), vals (nnz, val_dtype): device arrays, BORROWED like
  *   idx/vals of spmv_plan (the minor indices serve as idx); the plan builds and owns
  *   the pointer array on the device.  Other arguments as for spmv_plan_ex.
- * Synchronizes `stream` once.  Errors: SPMV_ERR_BAD_MATRIX when a major index is out
- * of range or the stream is not sorted by it, then the errors of spmv_plan_ex.
+ * With SPMV_PLAN_COO_UNSORTED the triples may come in any order: a stable device
+ * radix sort by (major, minor) puts them in storage order in a plan-owned copy, and
+ * rows, cols and vals are not read after the call returns.
+ * Synchronizes `stream` once.  Errors: SPMV_ERR_BAD_MATRIX when a major index (or,
+ * unsorted, either index) is out of range or a sorted stream is not sorted by the
+ * major index, SPMV_ERR_OOM, then the errors of spmv_plan_ex.
  */
 spmv_status spmv_plan_coo(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout,
                           const int32_t *rows, const int32_t *cols, const void *vals, int32_t val_dtype,

@@ -23,6 +23,7 @@ SPMV_CSC_WIDE, SPMV_CSR_TALL = 0, 1
 SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_F16 = 0, 1, 2, 3
 SPMV_OP_AX, SPMV_OP_VTA = 0, 1
 SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL, SPMV_PLAN_BANK_ORDER = 0x1, 0x2, 0x4, 0x8
+SPMV_PLAN_COO_UNSORTED = 0x10
 
 KERNEL_SCATTER, KERNEL_COMBINE, KERNEL_SEGDOT, KERNEL_FIXUP, KERNEL_DVALUES = 0, 1, 2, 3, 4
 
