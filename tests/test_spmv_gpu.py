@@ -191,6 +191,39 @@ def test_host_pointers_match_device():
     assert np.array_equal(u_host.astype(np.float64), u_dev)
 
 
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=str)
+def test_host_vectors_pinned_misaligned_or_pageable(layout, dtype):
+    """Host inputs and outputs of every kind (pinned, a pinned view off the 16-byte grid,
+    pageable) go through the staging buffers and agree with the device-vector results (the
+    segmented pass bit for bit) and with the oracle."""
+    m, n = (400, 30_000) if layout == "csc" else (30_000, 400)
+    A = synth.random_matrix(m, n, layout, density=0.01, seed=18)
+    plan, stored = make_plan(A, dtype)
+    vt = plan.vec_dtype
+    x = dev_vec(synth.uniform_vector(n, 1), vt)
+    v = dev_vec(synth.uniform_vector(m, 2), vt)
+    y_dev, u_dev = plan.spmv(x).cpu(), plan.spvtm(v).cpu()
+    seg_dev = u_dev if layout == "csc" else y_dev
+    for kind in ("pinned", "pinned_offset", "pageable"):
+        if kind == "pageable":
+            y_h, u_h = torch.empty(m, dtype=vt), torch.empty(n, dtype=vt)
+        else:
+            off = 1 if kind == "pinned_offset" else 0
+            y_h = torch.empty(m + off, dtype=vt, pin_memory=True)[off:]
+            u_h = torch.empty(n + off, dtype=vt, pin_memory=True)[off:]
+        for src in (x, x.cpu().pin_memory()):
+            pkg.spmv(plan.handle, src, y_h)
+            pkg.spvtm(plan.handle, v if src.is_cuda else v.cpu().pin_memory(), u_h)
+            plan.check()
+            xs, vs = host_of(x), host_of(v)
+            tol = TOL[dtype]
+            assert_close(y_h.double().numpy(), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), tol, kind)
+            assert_close(u_h.double().numpy(), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), tol, kind)
+            seg_host = u_h if layout == "csc" else y_h
+            assert torch.equal(seg_host, seg_dev), kind
+
+
 def test_segdot_is_bitwise_deterministic():
     A = synth.random_matrix(3000, 200_000, "csc", density=0.002, seed=10)
     plan, _ = make_plan(A, torch.float32)
