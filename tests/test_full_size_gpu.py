@@ -66,3 +66,24 @@ def test_wide_bf16_values_full_size():
 def test_tall_fp32_full_size():
     A = synth.tall_fp32_large(2, device=DEV)
     _check(A, None, "tall fp32")
+
+
+def test_wide_fp32_full_size_through_pinned_host_vectors():
+    """The end-to-end configuration of the benchmark: a bank-ordered plan and pinned host
+    vectors staged by the library."""
+    A = synth.wide_fp32_large(1, device=DEV)
+    stored, _ = _host(A)
+    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout="csc", flags=pkg.SPMV_PLAN_BANK_ORDER)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(12)
+    xh = (torch.rand(A.n, generator=g, device=DEV) * 2 - 1).cpu().pin_memory()
+    vh = (torch.rand(A.m, generator=g, device=DEV) * 2 - 1).cpu().pin_memory()
+    yh = torch.empty(A.m, pin_memory=True)
+    uh = torch.empty(A.n, pin_memory=True)
+    pkg.spmv(plan.handle, xh, yh)
+    pkg.spvtm(plan.handle, vh, uh)
+    plan.check()
+    xs, vs = xh.double().numpy(), vh.double().numpy()
+    assert_close(yh.double().numpy(), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, "host y = A x")
+    assert_close(uh.double().numpy(), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, "host u = v^T A")
+    plan.close()

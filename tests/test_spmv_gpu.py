@@ -224,6 +224,52 @@ def test_host_vectors_pinned_misaligned_or_pageable(layout, dtype):
             assert torch.equal(seg_host, seg_dev), kind
 
 
+@pytest.mark.parametrize("which", ["wide", "tall"])
+def test_host_vectors_on_large_plans(which):
+    """Pageable and pinned host vectors, and pinned long vectors with the short side on the
+    device, on power-law matrices of a few million nonzeros: all agree with the oracle, and
+    repeated calls agree bit for bit on the segmented pass."""
+    if which == "wide":
+        A = synth.wide_fp32_large(1, device="cuda", scale=0.06)
+    else:
+        A = synth.tall_fp32_large(2, device="cuda", scale=0.03)
+    stored = synth.SparseMatrix(A.layout, A.m, A.n, A.ptr.cpu().numpy(), A.idx.cpu().numpy(),
+                                A.vals.double().cpu().numpy())
+    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout=A.layout)
+    g = torch.Generator(device=DEV)
+    g.manual_seed(19)
+    x = (torch.rand(A.n, generator=g, device=DEV) * 2 - 1).cpu()
+    v = (torch.rand(A.m, generator=g, device=DEV) * 2 - 1).cpu()
+    xs, vs = x.double().numpy(), v.double().numpy()
+    y_ref, u_ref = oracle.spmv(stored, xs), oracle.spvtm(stored, vs)
+    y_sc, u_sc = oracle.abs_spmv(stored, xs), oracle.abs_spvtm(stored, vs)
+    seg = []
+    for kind in ("pageable", "pinned", "pinned", "pinned_short_on_device"):
+        pin = kind != "pageable"
+        xh, vh = (x.pin_memory(), v.pin_memory()) if pin else (x.clone(), v.clone())
+        yh, uh = torch.empty(A.m, pin_memory=pin), torch.empty(A.n, pin_memory=pin)
+        if kind == "pinned_short_on_device":  # the short side on the device, the long one pinned
+            if A.layout == "csc":
+                yd = torch.empty(A.m, device=DEV)
+                pkg.spmv(plan.handle, xh, yd)
+                yh = yd.cpu()
+                pkg.spvtm(plan.handle, v.to(DEV), uh)
+            else:
+                ud = torch.empty(A.n, device=DEV)
+                pkg.spvtm(plan.handle, vh, ud)
+                uh = ud.cpu()
+                pkg.spmv(plan.handle, x.to(DEV), yh)
+        else:
+            pkg.spmv(plan.handle, xh, yh)
+            pkg.spvtm(plan.handle, vh, uh)
+        plan.check()
+        assert_close(yh.double().numpy(), y_ref, y_sc, 1e-5, f"{which} {kind} y")
+        assert_close(uh.double().numpy(), u_ref, u_sc, 1e-5, f"{which} {kind} u")
+        if pin:
+            seg.append((uh if A.layout == "csc" else yh).clone())
+    assert torch.equal(seg[0], seg[1]) and torch.equal(seg[0], seg[2])
+
+
 def test_segdot_is_bitwise_deterministic():
     A = synth.random_matrix(3000, 200_000, "csc", density=0.002, seed=10)
     plan, _ = make_plan(A, torch.float32)
