@@ -160,4 +160,34 @@ def pin_gradients_fd(orc) -> None:
             assert abs(fd - gv[k]) <= 1e-7 * max(1.0, abs(gv[k])), "d/dvalues"
 
 
-ALL_PINS = [pin_dense_bruteforce, pin_dvalues_bruteforce, pin_adjoint_linearity, pin_closed_forms, pin_gradients_fd]
+def pin_cgls_least_squares(orc) -> None:
+    """CGLS from zero reaches numpy's least-squares solution (tall full rank) and the minimum-norm
+    solution (wide); its first step is the steepest-descent step on the normal equations, and its
+    k-th iterate the least-squares solution over the k-dimensional Krylov space."""
+    for m, n in ((60, 12), (12, 60)):
+        layout = "csr" if m > n else "csc"
+        A = random_matrix(m, n, layout, density=0.5, seed=31)
+        b = uniform_vector(m, 32)
+        D = dense_of(A)
+        x_ref = np.linalg.lstsq(D, b, rcond=None)[0]
+        x, rel = orc.cgls(A, b, np.zeros(n), iters=4 * min(m, n))
+        assert rel < 1e-8, "gradient norm"
+        assert np.allclose(x, x_ref, rtol=1e-7, atol=1e-9 * np.abs(x_ref).max()), "least-squares solution"
+        g = D.T @ b
+        alpha = g @ g / np.sum((D @ g) ** 2)
+        x1, _ = orc.cgls(A, b, np.zeros(n), iters=1)
+        assert np.allclose(x1, alpha * g, rtol=1e-12, atol=1e-15), "first step"
+        # the k-th iterate minimises ||b - A x|| over the Krylov space span{g, M g, ..., M^(k-1) g},
+        # M = A^T A (the defining property of CG on the normal equations)
+        M = D.T @ D
+        K = [g]
+        for k in (2, 3):
+            K.append(M @ K[-1])
+            B = np.stack(K, axis=1)
+            c = np.linalg.lstsq(D @ B, b, rcond=None)[0]
+            xk, _ = orc.cgls(A, b, np.zeros(n), iters=k)
+            assert np.allclose(xk, B @ c, rtol=1e-8, atol=1e-10 * np.abs(B @ c).max()), f"iterate {k}"
+
+
+ALL_PINS = [pin_dense_bruteforce, pin_dvalues_bruteforce, pin_adjoint_linearity, pin_closed_forms, pin_gradients_fd,
+            pin_cgls_least_squares]

@@ -117,3 +117,39 @@ def test_plan_mutant_is_caught(monkeypatch, mutant):
                 caught = True
                 break
     assert caught
+
+
+def _cgls_mutant(kind):
+    """CGLS recurrences with one plausible mistake, on the real products."""
+
+    def cgls(self, A, b, x0, iters):
+        x = np.array(x0, dtype=np.float64)
+        r = np.asarray(b, dtype=np.float64) - self.spmv(A, x)
+        s = self.spvtm(A, r)
+        p = s.copy()
+        gamma0 = gamma = float(s @ s)
+        for _ in range(iters):
+            q = self.spmv(A, p)
+            delta = float((p @ p) if kind == "alpha_denominator" else (q @ q))
+            alpha = gamma / delta if delta > 0 else 0.0
+            x += alpha * p
+            r = r + alpha * q if kind == "residual_sign" else r - alpha * q
+            s = self.spvtm(A, q if kind == "gradient_of_q" else r)
+            gamma_new = float(s @ s)
+            beta = (gamma / gamma_new if gamma_new > 0 else 0.0) if kind == "beta_inverted" else \
+                (gamma_new / gamma if gamma > 0 else 0.0)
+            gamma = gamma_new
+            p = s if kind == "no_momentum" else s + beta * p
+        return x, (np.sqrt(gamma / gamma0) if gamma0 > 0 else 0.0)
+
+    return cgls
+
+
+@pytest.mark.parametrize("kind", ["alpha_denominator", "residual_sign", "gradient_of_q", "beta_inverted",
+                                  "no_momentum"])
+def test_cgls_mutant_is_caught(monkeypatch, kind):
+    orc = oracle.Oracle()
+    pins.pin_cgls_least_squares(orc)  # the real recurrences pass
+    monkeypatch.setattr(oracle.Oracle, "cgls", _cgls_mutant(kind))
+    with pytest.raises(AssertionError):
+        pins.pin_cgls_least_squares(oracle.Oracle())
