@@ -151,5 +151,5 @@ def test_cgls_mutant_is_caught(monkeypatch, kind):
     orc = oracle.Oracle()
     pins.pin_cgls_least_squares(orc)  # the real recurrences pass
     monkeypatch.setattr(oracle.Oracle, "cgls", _cgls_mutant(kind))
-    with pytest.raises(AssertionError):
+    with pytest.raises(AssertionError), np.errstate(all="ignore"):  # some mutants diverge
         pins.pin_cgls_least_squares(oracle.Oracle())
