@@ -243,8 +243,9 @@ struct CooSort {
     }
 };
 
-// Sorts the triples by (major, minor), stably; fills the plan-owned minor/value arrays and the
-// sorted major indices (in the temporary block).  Returns the sorted major array or nullptr.
+// Sorts the triples by (major, minor), stably: the sorted minor indices and values go to the
+// plan-owned block, the sorted major indices to the temporary one; all three come back through
+// the out-parameters.  Range errors are reported through `err` (read by the caller after a sync).
 spmv_status coo_sort(CooSort &cs, const int32_t *major, const int32_t *minor, const void *vals, int sv, int64_t nnz,
                      int n_major, int n_minor, int grid, int32_t *err, cudaStream_t s, const int32_t **major_sorted,
                      int32_t **minor_sorted, void **vals_sorted) {

@@ -54,7 +54,7 @@ struct spmv_plan_s {
     void *hin = nullptr, *hout = nullptr, *hg = nullptr;
     void *ynorm = nullptr;  // A x of spmv_normal when the caller passes no buffer
     void *owned_ptr = nullptr;  // pointer array built by spmv_plan_coo (the other arrays stay borrowed)
-    void *owned_nz = nullptr;   // idx and vals in bank order (SPMV_PLAN_BANK_ORDER)
+    void *owned_nz = nullptr;   // plan-owned idx and vals: bank order, or triples sorted by spmv_plan_coo
     size_t owned_bytes = 0;
 
     // kernel timers (SPMV_PLAN_PROFILE)
