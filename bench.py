@@ -144,14 +144,42 @@ def pair_bytes(m, n, nnz, sv=4, sx=4, si=4, sp=4):
     return spmv_b, spvtm_b
 
 
-class OracleSample:
-    """A contiguous column block of A on the host, sized so that one FP64 oracle pair takes about `target_s`."""
+def host_cpu():
+    """(threads this process may use, CPU model string) of the host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return cores, f"{model or 'unknown'} ({os.uname().machine})"
 
-    def __init__(self, A, target_s: float):
+
+class OracleSample:
+    """A contiguous column block of A on the host, sized so that one FP64 oracle pair on
+    `threads` host threads takes about `target_s`."""
+
+    def __init__(self, A, target_s: float, threads: int = 1):
         import numpy as np
 
         import synth
 
+        self.threads = threads
         ptr = A.ptr.cpu().numpy().astype(np.int64)
         n = A.n
         cols = max(1, n // 64)
@@ -170,29 +198,42 @@ class OracleSample:
         b1, b2 = pair_bytes(A.m, cols, z)
         self.bytes = b1 + b2
 
-    def time_pair(self) -> float:
+    def time_pair(self, threads: int = None) -> float:
         import oracle
 
+        t = self.threads if threads is None else threads
         t0 = time.perf_counter()
-        oracle.spmv(self.S, self.x)
-        oracle.spvtm(self.S, self.v)
+        if t == 1:
+            oracle.spmv(self.S, self.x)
+            oracle.spvtm(self.S, self.v)
+        else:
+            oracle.spmv_mt(self.S, self.x, t)
+            oracle.spvtm_mt(self.S, self.v, t)
         return time.perf_counter() - t0
 
-    def describe(self, reps: int) -> str:
+    def describe(self, reps: int, threads: int = None) -> str:
+        t = self.threads if threads is None else threads
+        how = "single thread" if t == 1 else f"{t} threads (each a balanced column range; SpMV into per-thread y, summed)"
         return (f"FP64 oracle SpMV+SpVTM pair on the first {self.cols} of {self.n} columns ({self.z} nonzeros), "
-                f"{reps} pair(s), single thread, host {os.uname().machine}")
+                f"{reps} pair(s), {how}")
 
 
 def cpu_baseline(A, target_s: float):
-    smp = OracleSample(A, target_s / 4)
-    reps = 4
-    t = sum(smp.time_pair() for _ in range(reps)) / reps
-    return {"value": round(smp.bytes / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": smp.describe(reps)}
+    """The FP64 oracle pair on all host cores (the value) and on one core, on the same sample."""
+    cores, model = host_cpu()
+    smp = OracleSample(A, target_s / 6, threads=1)
+    reps1 = 2
+    t1 = sum(smp.time_pair(1) for _ in range(reps1)) / reps1
+    repsn = 6
+    smp.time_pair(cores)
+    tn = sum(smp.time_pair(cores) for _ in range(repsn)) / repsn
+    return {"value": round(smp.bytes / tn / 1e9, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": smp.describe(repsn, cores), "cpu_model": model,
+            "single_thread": {"value": round(smp.bytes / t1 / 1e9, 3), "cores": 1, "sample": smp.describe(reps1, 1)}}
 
 
 def run_reference(args):
-    """--impl reference: the FP64 oracle (plain CPU loops) on the same workload, rank 0 only."""
+    """--impl reference: the FP64 oracle (plain CPU loops) on the same workload, all host cores, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -200,10 +241,11 @@ def run_reference(args):
 
     import synth
 
+    cores, model = host_cpu()
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     A = synth.wide_fp32_large(1, device=dev)
     per_step = min(2.0, 150.0 / (args.steps + args.warmup))
-    smp = OracleSample(A, per_step)
+    smp = OracleSample(A, per_step, threads=cores)
     times = []
     for i in range(args.warmup + args.steps):
         t = smp.time_pair()
@@ -216,8 +258,8 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "m": A.m, "n": A.n, "nnz": A.nnz, "step": "one SpMV + one SpVTM",
                       "sample_columns": smp.cols, "sample_nnz": smp.z},
-           "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                            "sample": smp.describe(args.steps)},
+           "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                            "sample": smp.describe(args.steps), "cpu_model": model},
            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0

@@ -26,8 +26,10 @@
  *    [0, m) for CSC and [0, n) for CSR.  Repeated indices in one column (row)
  *    add up; indices need not be sorted; empty columns (rows) are allowed.
  *  - Element types (spmv_dtype): values and vectors are one of the pairs
- *    (F64, F64), (F32, F32), (BF16, F32), (F16, F32).  Accumulation is FP32 for
- *    the last three and FP64 for the first; cross-chunk combines are FP64.
+ *    (F64, F64), (F32, F32), (BF16, F32), (F16, F32).  Accumulation inside a
+ *    chunk is FP32 for the last three and FP64 for the first; the cross-chunk
+ *    combines (the sum of the per-CTA partial vectors of spmv, the overlap-zone
+ *    fix-up of spvtm) add in FP64 for every pair, in a fixed order.
  *  - A plan BORROWS the caller's device arrays ptr/idx/vals: they must stay
  *    allocated and unchanged (values may change between calls) until
  *    spmv_plan_destroy.  The plan owns only its workspace.
@@ -138,7 +140,9 @@ typedef struct {
  *   ptr, idx   device arrays (int32), see conventions; borrowed
  *   vals       device array of nnz values of type val_dtype; borrowed
  *   vec_dtype  element type of the dense vectors
- *   stream     cudaStream_t for the set-up kernels; the call synchronizes it once
+ *   stream     cudaStream_t for the set-up kernels; the call synchronizes it (a few
+ *              times: after validation, after the zone counts, at the end) and returns
+ *              with the plan ready
  *   flags      SPMV_PLAN_* bits
  * Errors: SPMV_ERR_INVALID_ARG, SPMV_ERR_BAD_MATRIX (checked unless
  * SPMV_PLAN_NO_VALIDATE), SPMV_ERR_OOM, SPMV_ERR_CUDA, SPMV_ERR_UNSUPPORTED.
@@ -204,7 +208,9 @@ spmv_status spvtm(spmv_plan_t plan, const void *v, void *u, void *stream);
  * op = SPMV_OP_VTA: U^T = V^T A with lengths m in, n out.  ld in elements,
  * ld >= vector length and ld * element size a multiple of 16.  Device pointers
  * only.  1 <= k <= 4096.  Every vector's result equals its single-vector
- * product within the stated tolerances.
+ * product within the stated tolerances.  The paper multiplies one vector at a
+ * time; the multi-vector form has no counterpart there (each vector's product
+ * is the Sec. III / Sec. IV-A computation).
  */
 spmv_status spmv_batch(spmv_plan_t plan, int32_t op, int32_t k, const void *in, int64_t ld_in,
                        void *out, int64_t ld_out, void *stream);
@@ -214,7 +220,8 @@ spmv_status spmv_batch(spmv_plan_t plan, int32_t op, int32_t k, const void *in, 
  * g[p] = r_i x_j for the nonzero at position p holding A_ij.  r has m entries,
  * x has n (vec_dtype); g has nnz entries of the plan's val_dtype.  This is the
  * d(values) part of the backward pass of y = A x (with r = dL/dy); the dx part
- * is spvtm(plan, r).  Device or host pointers.
+ * is spvtm(plan, r).  Device or host pointers.  No counterpart in the paper
+ * (the gradient of the product, computed with the plan's Sec. II partition).
  */
 spmv_status spmv_dvalues(spmv_plan_t plan, const void *r, const void *x, void *g, void *stream);
 
@@ -260,7 +267,11 @@ spmv_status spmv_profile_enable(spmv_plan_t plan, int32_t on);
  * or events).  The first call on a device resolves the array's device address
  * (set-up), so make that first call before any stream capture.  Nothing is
  * allocated; an m above 49152 or a bad size is rejected with
- * SPMV_ERR_INVALID_ARG before any launch.  Indices outside [0, m) are skipped.
+ * SPMV_ERR_INVALID_ARG before any launch.  The matrix is not validated and
+ * device-side problems are not reported (there is no error word to read back):
+ * a nonzero whose row index lies outside [0, m) is skipped, and a malformed ptr
+ * never makes the kernel read outside ptr[0..n], idx, vals or x[0..n), but the
+ * result is then unspecified.
  */
 spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, const int32_t *idx,
                          const float *vals, const float *x, float *y, void *stream);
@@ -299,7 +310,9 @@ const char *spmv_last_error(void);
 const char *spmv_version(void);
 
 /* ------------------------------------------------------------------------ */
-/* Serving: continuous batching of single products over resident matrices. */
+/* Serving: continuous batching of single products over resident matrices.
+ * The paper has no serving layer; every product a server runs is the spmv /
+ * spvtm / spmv_batch computation above. */
 
 typedef struct serve_s *serve_t;
 

@@ -6,7 +6,9 @@ shares no code with the CUDA path; both receive their inputs from the seeded
 generators in ``synth``.
 
 * ``spmv`` / ``spvtm`` / ``dvalues`` call straight FP64 loops in ``oracle.c``
-  (Sec. I problem statement, Sec. II storage orders).
+  (Sec. I problem statement, Sec. II storage orders); ``spmv_mt`` / ``spvtm_mt``
+  run the same loops over balanced column (row) ranges on several host threads,
+  for timing the CPU baseline on all cores.
 * :mod:`oracle.plan` restates the nonzero partition of Sec. II and the
   overlap-zone set-up of Sec. IV-B step by step.
 
@@ -30,7 +32,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+CFLAGS = ["-O2", "-std=c99", "-fPIC", "-shared", "-pthread", "-ffp-contract=off", "-fno-fast-math"]
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +63,11 @@ def _declare(lib):
         f = getattr(lib, name)
         f.argtypes = [i64, i64, p, p, p, p, p]
         f.restype = None
+    for name in ("oracle_csc_matvec_mt", "oracle_csc_vecmat_mt", "oracle_csr_matvec_mt", "oracle_csr_vecmat_mt"):
+        f = getattr(lib, name, None)
+        if f is not None:  # absent from mutant builds that predate them
+            f.argtypes = [i64, i64, p, p, p, p, p, ctypes.c_int]
+            f.restype = ctypes.c_int
     return lib
 
 
@@ -110,6 +117,27 @@ class Oracle:
         f = "oracle_csc_vecmat" if A.layout == "csc" else "oracle_csr_vecmat"
         assert len(v) == A.m
         return self._run(f, A, v, A.n)
+
+    def _run_mt(self, fname, A, vec_in, out_len, threads):
+        ptr, idx, val = _i32(A.ptr), _i32(A.idx), _f64(A.vals)
+        vin = _f64(vec_in)
+        out = np.empty(out_len, dtype=np.float64)
+        rc = getattr(self.lib, fname)(A.m, A.n, _ptr(ptr), _ptr(idx), _ptr(val), _ptr(vin), _ptr(out), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"{fname}: could not start {threads} threads")
+        return out
+
+    def spmv_mt(self, A, x, threads: int) -> np.ndarray:
+        """y = A x on `threads` host threads (the serial loop over balanced column/row ranges)."""
+        f = "oracle_csc_matvec_mt" if A.layout == "csc" else "oracle_csr_matvec_mt"
+        assert len(x) == A.n
+        return self._run_mt(f, A, x, A.m, threads)
+
+    def spvtm_mt(self, A, v, threads: int) -> np.ndarray:
+        """u = (v^T A)^T on `threads` host threads."""
+        f = "oracle_csc_vecmat_mt" if A.layout == "csc" else "oracle_csr_vecmat_mt"
+        assert len(v) == A.m
+        return self._run_mt(f, A, v, A.n, threads)
 
     def dvalues(self, A, r, x) -> np.ndarray:
         """g[k] = r_i x_j for the stored nonzero k = A_ij (gradient of r^T A x)."""
@@ -174,6 +202,14 @@ def spvtm(A, v):
 
 def dvalues(A, r, x):
     return _get().dvalues(A, r, x)
+
+
+def spmv_mt(A, x, threads):
+    return _get().spmv_mt(A, x, threads)
+
+
+def spvtm_mt(A, v, threads):
+    return _get().spvtm_mt(A, v, threads)
 
 
 def least_squares(A, x, b):

@@ -5,6 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 namespace gbk {
 
 // Kernel modes of the streaming kernel (one staged pass over the nonzeros).
@@ -68,6 +71,31 @@ struct StreamParams {
     void *rec_left, *rec_right;  // SEGDOT carry records [b * ntiles + t]: (hi, lo) pairs of the accumulation type
     int32_t *err;
 };
+
+// Dynamic shared-memory limit of one kernel, raised at most once per device and
+// size: the value set so far on each device, read without a lock, raised under it.
+constexpr int MAX_DEVICES = 64;
+struct SmemLimit {
+    std::atomic<int> bytes[MAX_DEVICES];
+    std::mutex mu;
+    SmemLimit() {
+        for (auto &b : bytes) b.store(0, std::memory_order_relaxed);
+    }
+};
+// Make `kern` launchable with `smem` bytes of dynamic shared memory on the current device.
+template <typename K>
+cudaError_t ensure_smem_limit(K kern, SmemLimit &lim, int smem) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    if (lim.bytes[dev].load(std::memory_order_acquire) >= smem) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(lim.mu);
+    if (lim.bytes[dev].load(std::memory_order_relaxed) >= smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) lim.bytes[dev].store(smem, std::memory_order_release);
+    return e;
+}
 
 struct LaunchArgs {
     StreamParams sp;

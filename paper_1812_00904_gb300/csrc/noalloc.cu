@@ -8,6 +8,10 @@
 // this library's static device memory; the existing fixed-order combine
 // kernel then sums the partials in FP64 into y.
 //
+// Nothing is checked on the device: an index outside [0, m) is skipped, and
+// the column walks never leave [0, n) even when ptr is malformed, but neither
+// is reported (the call allocates nothing, not even an error word to read back).
+//
 // The scratch array is a file-scope __device__ array: every device that loads
 // the library holds it (16 MiB) until the process exits, and every call shares
 // it, so calls that overlap on the GPU race on it.  Each call overwrites the
@@ -35,7 +39,7 @@ static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS]
 // ends with a shuffle binary search.
 __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_scatter_kernel(
     const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, const float *__restrict__ vals,
-    const float *__restrict__ x, int m, int n, int nnz, float *__restrict__ part, int32_t *err) {
+    const float *__restrict__ x, int m, int n, int nnz, float *__restrict__ part) {
     extern __shared__ float acc[];
     for (int i = threadIdx.x; i < m; i += blockDim.x) acc[i] = 0.f;
     __syncthreads();
@@ -49,7 +53,7 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_scatter_kernel(
     const int we = wb + wq + (warp < wr ? 1 : 0);
     if (wb < we) {
         // column holding nonzero wb: the last j with ptr[j] <= wb
-        int lo = 0, hi = n;
+        int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = lo + (hi - lo + 1) / 2;
             if (ptr[mid] <= wb)
@@ -57,10 +61,10 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_scatter_kernel(
             else
                 hi = mid - 1;
         }
-        int col = lo;
+        int col = lo;  // in [0, n - 1] (n >= 1 here)
         for (int base = wb; base < we; base += 32) {
             const int k = base + lane;
-            while (ptr[col + 1] <= base) ++col;  // warp-uniform: column holding position base
+            while (col + 1 < n && ptr[col + 1] <= base) ++col;  // warp-uniform: column holding position base
             const int ej = (col + 1 + lane <= n) ? ptr[col + 1 + lane] : INT_MAX;  // end of column col + lane
             int cnt = 0;  // number of those ends at or before k
 #pragma unroll
@@ -70,14 +74,11 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_scatter_kernel(
             }
             const int e31 = __shfl_sync(0xffffffffu, ej, 31);
             if (cnt == 31 && e31 <= k) cnt = 32;
-            int mycol = col + cnt;
+            int mycol = min(col + cnt, n - 1);
             if (k < we) {
-                while (ptr[mycol + 1] <= k) ++mycol;  // only past runs of empty columns
+                while (mycol + 1 < n && ptr[mycol + 1] <= k) ++mycol;  // only past runs of empty columns
                 const int row = idx[k];
-                if (static_cast<unsigned>(row) < static_cast<unsigned>(m))
-                    atomicAdd(&acc[row], vals[k] * x[mycol]);
-                else
-                    atomicOr(err, 1);
+                if (static_cast<unsigned>(row) < static_cast<unsigned>(m)) atomicAdd(&acc[row], vals[k] * x[mycol]);
             }
         }
     }
@@ -86,11 +87,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) noalloc_scatter_kernel(
     for (int i = threadIdx.x; i < m; i += blockDim.x) dst[i] = acc[i];
 }
 
-static __device__ int32_t g_noalloc_err;
-
 struct NoallocDevice {
     float *scratch = nullptr;
-    int32_t *err = nullptr;
     int sms = 0;
     bool ready = false;
 };
@@ -120,17 +118,15 @@ extern "C" spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int
         // first call on this device: resolve the device address of the static scratch
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         if (!D.ready) {
-            void *a = nullptr, *e = nullptr;
+            void *a = nullptr;
             cudaError_t r1 = cudaGetSymbolAddress(&a, g_noalloc_scratch);
-            cudaError_t r2 = cudaGetSymbolAddress(&e, g_noalloc_err);
             int sms = 0;
             cudaError_t r3 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             cudaError_t r4 = cudaFuncSetAttribute(noalloc_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   NOALLOC_MAX_M * (int)sizeof(float));
-            if (r1 != cudaSuccess || r2 != cudaSuccess || r3 != cudaSuccess || r4 != cudaSuccess)
+            if (r1 != cudaSuccess || r3 != cudaSuccess || r4 != cudaSuccess)
                 return set_error(SPMV_ERR_CUDA, "spmv_noalloc: device set-up failed");
             D.scratch = static_cast<float *>(a);
-            D.err = static_cast<int32_t *>(e);
             D.sms = sms;
             D.ready = true;
         }
@@ -142,7 +138,7 @@ extern "C" spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int
     }
     const int P = (int)std::max<int64_t>(1, std::min<int64_t>(D.sms, (int64_t)(NOALLOC_SCRATCH_FLOATS / (size_t)m)));
     noalloc_scatter_kernel<<<P, NOALLOC_THREADS, (size_t)m * sizeof(float), s>>>(ptr, idx, vals, x, (int)m, (int)n,
-                                                                                  (int)nnz, D.scratch, D.err);
+                                                                                  (int)nnz, D.scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(SPMV_ERR_CUDA, std::string("spmv_noalloc: ") + cudaGetErrorString(e));
     void *outs[1] = {y};

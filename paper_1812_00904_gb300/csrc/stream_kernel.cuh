@@ -702,18 +702,15 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     }
 }
 
-// Host-side launch of one instantiation; sets the shared-memory limit once per kernel.
+// Host-side launch of one instantiation; raises its shared-memory limit once per device.
 // Up to WARPS_REGS warps run a kernel compiled for 128 registers a thread; more warps
 // (single-vector passes only) run one compiled for 80.
 template <typename VT, typename XT, int MODE, int KB, bool SMEMV, int WB>
 cudaError_t launch_wb(const LaunchArgs &a) {
     auto kern = stream_kernel<VT, XT, MODE, KB, SMEMV, WB>;
-    static int configured = 0;
-    if (configured < a.smem) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.smem);
-        if (e != cudaSuccess) return e;
-        configured = a.smem;
-    }
+    static SmemLimit lim;
+    const cudaError_t e = ensure_smem_limit(kern, lim, a.smem);
+    if (e != cudaSuccess) return e;
     kern<<<a.grid, a.block, a.smem, a.stream>>>(a.sp);
     return cudaGetLastError();
 }

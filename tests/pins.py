@@ -189,5 +189,23 @@ def pin_cgls_least_squares(orc) -> None:
             assert np.allclose(xk, B @ c, rtol=1e-8, atol=1e-10 * np.abs(B @ c).max()), f"iterate {k}"
 
 
+def pin_threaded_loops(orc) -> None:
+    """The all-core loops equal the dense products exactly on integer data, for thread counts
+    below, at and above the number of columns (rows); the dot-product directions equal the
+    serial loop bit for bit on random data too (one thread computes each entry)."""
+    for A in _int_cases():
+        D = dense_of(A)
+        x = uniform_vector(A.n, 17, int_values=6)
+        v = uniform_vector(A.m, 18, int_values=6)
+        for t in (1, 2, 3, 7, 16):
+            assert np.array_equal(orc.spmv_mt(A, x, t), D @ x), f"spmv_mt({t}) != dense ({A.name})"
+            assert np.array_equal(orc.spvtm_mt(A, v, t), v @ D), f"spvtm_mt({t}) != dense ({A.name})"
+    for layout in ("csc", "csr"):
+        A = random_matrix(120, 900, layout, density=0.03, seed=31)
+        x, v = uniform_vector(A.n, 32), uniform_vector(A.m, 33)
+        dot_mt, dot = (orc.spvtm_mt(A, v, 5), orc.spvtm(A, v)) if layout == "csc" else (orc.spmv_mt(A, x, 5), orc.spmv(A, x))
+        assert np.array_equal(dot_mt, dot), f"dot-product direction differs from the serial loop ({layout})"
+
+
 ALL_PINS = [pin_dense_bruteforce, pin_dvalues_bruteforce, pin_adjoint_linearity, pin_closed_forms, pin_gradients_fd,
-            pin_cgls_least_squares]
+            pin_cgls_least_squares, pin_threaded_loops]

@@ -34,6 +34,10 @@ C_MUTANTS = {
     # gradient with x of the row index instead of the column
     "csc_dvalues_index": ("g[k] = r[idx[k]] * x[j];", "g[k] = r[idx[k]] * x[idx[k] % n];"),
     "csr_dvalues_index": ("g[k] = r[i] * x[idx[k]];", "g[k] = r[idx[k] % m] * x[idx[k]];"),
+    # all-core loops: the last thread's private copy left out of the final sum
+    "mt_sum_drops_thread": ("for (int t = 0; t < threads; ++t) s += priv", "for (int t = 0; t + 1 < threads; ++t) s += priv"),
+    # all-core loops: neighbouring ranges skip the column (row) between them
+    "mt_range_gap": ("if (t > 0) J->lo = jobs[t - 1].hi;", "if (t > 0) J->lo = jobs[t - 1].hi + (jobs[t - 1].hi < n_major);"),
 }
 
 
