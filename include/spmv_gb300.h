@@ -140,9 +140,9 @@ typedef struct {
  *   ptr, idx   device arrays (int32), see conventions; borrowed
  *   vals       device array of nnz values of type val_dtype; borrowed
  *   vec_dtype  element type of the dense vectors
- *   stream     cudaStream_t for the set-up kernels; the call synchronizes it (a few
- *              times: after validation, after the zone counts, at the end) and returns
- *              with the plan ready
+ *   stream     cudaStream_t for the set-up kernels; the call synchronizes it (after
+ *              validation, after the bank-order copy when asked for, and at the end)
+ *              and returns with the plan ready
  *   flags      SPMV_PLAN_* bits
  * Errors: SPMV_ERR_INVALID_ARG, SPMV_ERR_BAD_MATRIX (checked unless
  * SPMV_PLAN_NO_VALIDATE), SPMV_ERR_OOM, SPMV_ERR_CUDA, SPMV_ERR_UNSUPPORTED.

@@ -52,6 +52,7 @@ cudaError_t launch_stream(const spmv_plan_s *p, int mode, int kb, const LaunchAr
 }
 
 int kb_template(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : 8; }
+int kb_log2(int kbt) { return kbt <= 1 ? 0 : kbt <= 2 ? 1 : kbt <= 4 ? 2 : 3; }
 
 // Kernel timers: bracket one launch with events when the plan profiles.
 struct ProfScope {
@@ -229,14 +230,17 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
         a.sp.vout[b] = out[b];
     }
     set_geometry(p, a, MODE_SEGDOT, kb_template(kb));
+    const spmv_plan_s::ProcZones &pz = p->pz[kb_log2(kb_template(kb))];
+    if (pz.W * 32 != a.block) return set_error(SPMV_ERR_CUDA, "internal: zone table made for another warp count");
+    a.sp.nproc = pz.nproc;
     a.stream = s;
     {
         ProfScope ps(p, 2, s);
         CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
     }
-    if (p->tz > 0) {
+    if (pz.z > 0) {
         ProfScope ps(p, 3, s);
-        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, p->tzones, p->tz, p->rec_left, p->rec_right, p->ntiles, kb, out, s));
+        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, pz.zones, pz.z, p->rec_left, p->rec_right, pz.nproc, kb, out, s));
     }
     return SPMV_OK;
 }
@@ -453,7 +457,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     const size_t o_aux = carve((size_t)p->P * sizeof(ChunkAux));
     const size_t o_chunks = carve((size_t)p->P * sizeof(ChunkDev));
     const size_t o_zones = carve((size_t)p->P * sizeof(ZoneDev));
-    const size_t o_counts = carve(64);
+    const size_t o_counts = carve(128);
     const size_t o_err = carve(16);
     const size_t ws1 = off;
     CUDA_TRY(cudaMalloc(&p->ws, ws1));
@@ -464,7 +468,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->zones = reinterpret_cast<ZoneDev *>(w1 + o_zones);
     p->counts = reinterpret_cast<int32_t *>(w1 + o_counts);
     p->err = reinterpret_cast<int32_t *>(w1 + o_err);
-    CUDA_TRY(cudaMemsetAsync(p->counts, 0, 64, s));
+    CUDA_TRY(cudaMemsetAsync(p->counts, 0, 128, s));
     CUDA_TRY(cudaMemsetAsync(p->err, 0, 16, s));
 
     // ---- structural checks
@@ -511,27 +515,40 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     CUDA_TRY(launch_pad_ptr(ptr, p->pptr, p->n_major, (int)nnz, p->pptr_len, s));
     CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, p->P, nullptr, p->T, p->aux, s));
     CUDA_TRY(launch_setup(p->aux, p->P, p->chunks, p->zones, p->counts, s));
-    int32_t counts[4] = {0, 0, 0, 0};
-    CUDA_TRY(cudaMemcpyAsync(counts, p->counts, 16, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    p->z = counts[0];
-    p->vmax = counts[2];
     p->ntiles = (int)nt64;
 
-    // ---- workspace, part 2: tiles (descriptors, masks, zones, records) and partial sums
+    // ---- workspace, part 2: tiles (descriptors, masks), processor zones, records and partial sums
     const int nt = p->ntiles;
-    const size_t part_bytes = p->onchip ? (size_t)std::max(1, std::min(sms, nt)) * p->batch_width * p->n_minor * p->sa
+    p->ctas = std::max(1, std::min(sms, nt));
+    // processors (warps holding tiles) of the segmented passes, per vector-slot template in use
+    const int ntpl = p->onchip ? kb_log2(kb_template(p->batch_width)) + 1 : 1;
+    std::vector<std::vector<int32_t>> pnzb(ntpl);
+    p->max_nproc = 1;
+    for (int i = 0; i < ntpl; ++i) {
+        spmv_plan_s::ProcZones &pz = p->pz[i];
+        pz.W = std::max(1, warps_for(p, MODE_SEGDOT, 1 << i));
+        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, nullptr);
+        pnzb[i].resize((size_t)pz.nproc + 1);
+        stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, pnzb[i].data());
+        p->max_nproc = std::max(p->max_nproc, pz.nproc);
+    }
+    const size_t part_bytes = p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
                                         : (size_t)p->n_minor * sizeof(double);
+    const size_t rec_bytes = (size_t)p->batch_width * p->max_nproc * 2 * p->sa;
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
-    const size_t o_tz = carve((size_t)std::max(nt, 1) * sizeof(ZoneDev));
-    const size_t o_recl = carve((size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa);
-    const size_t o_recr = carve((size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa);
+    size_t o_pz[4];
+    for (int i = 0; i < ntpl; ++i) o_pz[i] = carve((size_t)std::max(p->pz[i].nproc, 1) * sizeof(ZoneDev));
+    const size_t o_recl = carve(rec_bytes);
+    const size_t o_recr = carve(rec_bytes);
     const size_t o_part = carve(std::max(part_bytes, (size_t)16));
-    const size_t o_tnzb = carve((size_t)(nt + 1) * 4);  // set-up only
+    // set-up only
+    const size_t o_tnzb = carve((size_t)(nt + 1) * 4);
     const size_t o_taux = carve((size_t)std::max(nt, 1) * sizeof(ChunkAux));
-    const size_t o_tdev = carve((size_t)std::max(nt, 1) * sizeof(ChunkDev));
+    const size_t o_pnzb = carve((size_t)(p->max_nproc + 1) * 4 * ntpl);
+    const size_t o_paux = carve((size_t)p->max_nproc * sizeof(ChunkAux));
+    const size_t o_pdev = carve((size_t)p->max_nproc * sizeof(ChunkDev));
     const size_t ws2 = off;
     CUDA_TRY(cudaMalloc(&p->ws2, ws2));
     p->ws_bytes = ws1 + ws2;
@@ -541,27 +558,36 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     p->rec_left = w2 + o_recl;
     p->rec_right = w2 + o_recr;
     p->part = w2 + o_part;
-    // the same Sec. IV-B set-up over the execution tiles gives the tile-level overlap zones
     int32_t *tnzb = reinterpret_cast<int32_t *>(w2 + o_tnzb);
     ChunkAux *taux = reinterpret_cast<ChunkAux *>(w2 + o_taux);
-    ChunkDev *tdev = reinterpret_cast<ChunkDev *>(w2 + o_tdev);
-    p->tzones = reinterpret_cast<ZoneDev *>(w2 + o_tz);
-    p->tz = 0;
+    int32_t *dpnzb = reinterpret_cast<int32_t *>(w2 + o_pnzb);
+    ChunkAux *paux = reinterpret_cast<ChunkAux *>(w2 + o_paux);
+    ChunkDev *pdev = reinterpret_cast<ChunkDev *>(w2 + o_pdev);
     if (nt > 0) {
+        // execution tiles: bounds, first/last segments, owned end events; masks and descriptors
         CUDA_TRY(launch_tile_bounds(nt, p->T, (int)nnz, tnzb, s));
         CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, nt, tnzb, p->T, taux, s));
-        CUDA_TRY(launch_setup(taux, nt, tdev, p->tzones, p->counts + 4, s));
-        int32_t tc[4] = {0, 0, 0, 0};
-        CUDA_TRY(cudaMemcpyAsync(tc, p->counts + 4, 16, cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        p->tz = tc[0];
+        CUDA_TRY(launch_masks(p->pptr, taux, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
+        // the Sec. IV-B set-up over the processors of the segmented passes gives their overlap zones
+        for (int i = 0; i < ntpl; ++i) {
+            spmv_plan_s::ProcZones &pz = p->pz[i];
+            pz.zones = reinterpret_cast<ZoneDev *>(w2 + o_pz[i]);
+            int32_t *nzb_i = dpnzb + (size_t)i * (p->max_nproc + 1);
+            CUDA_TRY(cudaMemcpyAsync(nzb_i, pnzb[i].data(), ((size_t)pz.nproc + 1) * 4, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, pz.nproc, nzb_i, p->T, paux, s));
+            CUDA_TRY(launch_setup(paux, pz.nproc, pdev, pz.zones, p->counts + 8 + 4 * i, s));
+        }
     }
-    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, (size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa, s));
-    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, (size_t)p->batch_width * std::max(nt, 1) * 2 * p->sa, s));
-    CUDA_TRY(launch_masks(p->pptr, tdev, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
-    p->ctas = std::max(1, std::min(sms, nt));
+    CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, rec_bytes, s));
+    CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, rec_bytes, s));
     CUDA_TRY(cudaEventRecord(e1, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
+    // zone counts of the reporting chunks ([0] z, [2] V) and of the processor tables ([8 + 4i])
+    int32_t counts[32] = {0};
+    CUDA_TRY(cudaMemcpyAsync(counts, p->counts, sizeof(counts), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // also keeps pnzb alive until its copies are done
+    p->z = counts[0];
+    p->vmax = counts[2];
+    for (int i = 0; i < ntpl; ++i) p->pz[i].z = nt > 0 ? counts[8 + 4 * i] : 0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);

@@ -68,7 +68,8 @@ struct StreamParams {
     const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
     void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g
     void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
-    void *rec_left, *rec_right;  // SEGDOT carry records [b * ntiles + t]: (hi, lo) pairs of the accumulation type
+    void *rec_left, *rec_right;  // SEGDOT carry records [b * nproc + proc]: (hi, lo) pairs of the accumulation type
+    int32_t nproc;           // processors (warps holding tiles) of this launch: the record stride
     int32_t *err;
 };
 
@@ -115,6 +116,9 @@ cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int np
                            void *const *out, cudaStream_t s);
 cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s);
+// Processors of a streaming launch: the warps that hold tiles, in order (the kernel's
+// numbering).  Fills nzb[0..nproc] with their nonzero boundaries; returns nproc.
+int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int32_t *nzb);
 
 // Plan kernels (plan.cu).
 cudaError_t launch_validate(const int32_t *ptr, const int32_t *idx, int n_major, int nnz, int n_minor, int32_t *err,
@@ -127,8 +131,9 @@ cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, cons
 cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s);
 // Execution tile boundaries tile_nzb[t] = min(t * T, nnz), t = 0..ntiles.
 cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cudaStream_t s);
-// Per tile: segment-start masks and the kernel's tile descriptors (flags from the tile-level set-up).
-cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles, int nnz, int n_major, int mwp,
+// Per tile: segment-start masks and the kernel's tile descriptors (needLeft / needRight of
+// every tile from its neighbours' first and last segments).
+cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles, int nnz, int n_major, int mwp,
                          uint32_t *masks, TileMeta *meta, cudaStream_t s);
 
 }  // namespace gbk

@@ -275,16 +275,18 @@ cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cu
 // One warp per tile: the segment-start bits of the tile (bit pos set when a
 // segment j in (i0, i1] starts at nonzero kb0 + pos, pos < nze - kb0, kb0 =
 // nzb rounded down to 8) and the tile descriptor read by the streaming kernel.
-// Flag bit 2 marks a tile in which an empty segment ends (then several
+// Flags: needLeft / needRight of the tile, from its neighbours' last and first
+// segments (the "determine overlap zones" step of Sec. IV-B; tiles are never
+// empty); bit 2 marks a tile in which an empty segment ends (then several
 // segments can start at one position and the kernels take their general path).
-__global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *__restrict__ tiles, int ntiles, int nnz,
+__global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkAux *__restrict__ tiles, int ntiles, int nnz,
                              int n_major, int mwp, uint32_t *__restrict__ masks, TileMeta *__restrict__ meta) {
     __shared__ uint32_t sm[8][32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int t = blockIdx.x * 8 + wib;
     if (t >= ntiles) return;
-    const ChunkDev d = tiles[t];
+    const ChunkAux d = tiles[t];
     const int kb0 = d.nz_begin & ~7;
     const int rel_hi = d.nz_end - kb0;
     sm[wib][lane] = 0u;
@@ -303,7 +305,9 @@ __global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *_
         TileMeta m;
         m.nzb = d.nz_begin;
         m.e_begin = d.e_begin;
-        m.flags = (d.flags & 3) | (dup ? 4 : 0);
+        const bool need_left = t > 0 && tiles[t - 1].jl == d.jf;
+        const bool need_right = t + 1 < ntiles && tiles[t + 1].jf == d.jl;
+        m.flags = (need_left ? 1 : 0) | (need_right ? 2 : 0) | (dup ? 4 : 0);
         m.pad = 0;
         meta[t] = m;
         if (t == ntiles - 1) {
@@ -317,11 +321,33 @@ __global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkDev *_
     }
 }
 
-cudaError_t launch_masks(const int32_t *pptr, const ChunkDev *tiles, int ntiles, int nnz, int n_major, int mwp,
+cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles, int nnz, int n_major, int mwp,
                          uint32_t *masks, TileMeta *meta, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
     masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, tiles, ntiles, nnz, n_major, mwp, masks, meta);
     return cudaGetLastError();
+}
+
+// The warps of a streaming launch that hold tiles, in the kernel's order: CTA g takes
+// tiles [ta, ta + nct) by the Sec. II rule over the grid, its warp w the same rule
+// over its W warps.  nzb[q] = first nonzero of processor q; nzb[nproc] = nnz.
+int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int32_t *nzb) {
+    if (ctas < 1 || W < 1) return 0;
+    const int tq = ntiles / ctas, tr = ntiles % ctas;
+    int np = 0;
+    for (int g = 0; g < ctas; ++g) {
+        const int ta = g * tq + (g < tr ? g : tr);
+        const int nct = tq + (g < tr ? 1 : 0);
+        for (int w = 0; w < W; ++w) {
+            const int nk = nct / W + (w < nct % W ? 1 : 0);
+            if (nk == 0) continue;
+            const int wa = ta + w * (nct / W) + (w < nct % W ? w : nct % W);
+            if (nzb) nzb[np] = (int)((int64_t)wa * T < nnz ? (int64_t)wa * T : nnz);
+            ++np;
+        }
+    }
+    if (nzb) nzb[np] = nnz;
+    return np;
 }
 
 // Plan-owned copy of the nonzeros, permuted within every major segment (a column of a

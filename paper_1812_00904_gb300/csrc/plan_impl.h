@@ -42,10 +42,20 @@ struct spmv_plan_s {
     int32_t *err = nullptr;
     gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
     uint32_t *masks = nullptr;
-    gbk::ZoneDev *tzones = nullptr;        // tile-level overlap zones
+    // Overlap zones among the processors of the segmented passes (the warps that hold
+    // tiles, Sec. II groups of whole tiles), one table per vector-slot template of the
+    // passes (index log2 kbt: 1, 2, 4, 8 vectors), since the warp count can differ.
+    struct ProcZones {
+        int W = 0;      // warps per CTA of those passes
+        int nproc = 0;  // processors, the stride of the carry records
+        int z = 0;      // overlap zones among them
+        gbk::ZoneDev *zones = nullptr;
+    };
+    ProcZones pz[4];
+    int max_nproc = 0;
     void *rec_left = nullptr, *rec_right = nullptr;  // (hi, lo) pairs of the accumulation type
     void *part = nullptr;
-    int z = 0, vmax = 0, tz = 0;
+    int z = 0, vmax = 0;
     double setup_ms = 0.0;
     int64_t max_chunk = 0, min_chunk = 0;
 

@@ -1,6 +1,7 @@
-// Streaming kernel: the nonzeros are cut into equal-count tiles (the Sec. II
-// partition, every tile a "processor"); each CTA takes a contiguous range of
-// tiles by the same rule, and within a CTA warp w takes tiles w, w + W, w + 2W, ...
+// Streaming kernel: the nonzeros are cut into equal-count tiles of T nonzeros;
+// each CTA takes a contiguous range of tiles by the Sec. II rule, and within a
+// CTA every warp takes a contiguous sub-range by the same rule: the warps are the
+// "processors" of Sec. II (each a contiguous, equally sized group of nonzeros).
 // Every warp streams its own tiles through S shared-memory slots of its own:
 // when it has finished a tile it issues the bulk (TMA) copies of the tile S
 // ahead into the freed slot (one copy per array: indices, values, segment-start
@@ -17,10 +18,12 @@
 //                 (wide CSC y = A x; tall CSR u = v^T A by role reversal), into
 //                 an on-chip copy of the short vector per CTA.
 //   MODE_SEGDOT:  out[j] = sum_k val[k] * w[idx[k]] over segment j -- v^T A_(i)
-//                 of Sec. IV-A (wide CSC u^T = v^T A; tall CSR y = A x).  The
-//                 first and last segments of a tile that continue in its
-//                 neighbours (overlap zones) leave their partial sums in carry
-//                 records for the zone fixup.
+//                 of Sec. IV-A (wide CSC u^T = v^T A; tall CSR y = A x).  A
+//                 segment that runs on from one of a warp's tiles into the next
+//                 is carried in registers; the first and last segments of a
+//                 warp's range that continue in the neighbouring warps (overlap
+//                 zones) leave their partial sums in the warp's carry records
+//                 for the zone fixup.
 //   MODE_DVALUES: g[k] = minor[idx[k]] * major[seg(k)].
 #pragma once
 
@@ -73,12 +76,18 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
     unsigned char *myslots = smem + p.vec_region_bytes + BAR_BYTES + (size_t)warp * S * p.slot_bytes;
 
-    // this CTA's tiles: the Sec. II rule over the grid; this warp's: ta + warp + k W
+    // this CTA's tiles: the Sec. II rule over the grid; this warp's: the same rule over the
+    // CTA's W warps, tiles wa .. wa + nk - 1
     const int G = gridDim.x, g = blockIdx.x;
     const int tq = p.ntiles / G, tr = p.ntiles % G;
     const int ta = g * tq + min(g, tr);
-    const int tb = ta + tq + (g < tr ? 1 : 0);
-    const int nk = (tb - ta > warp) ? (tb - ta - warp + W - 1) / W : 0;
+    const int nct = tq + (g < tr ? 1 : 0);
+    const int wa = ta + warp * (nct / W) + min(warp, nct % W);
+    const int nk = nct / W + (warp < nct % W ? 1 : 0);
+    // processor number of this warp among the warps that hold tiles (the index of its
+    // carry records): all W warps of every CTA when every CTA has at least W tiles,
+    // else one tile per warp, numbered like the tiles
+    const int proc = (tq >= W) ? g * W + warp : wa;
 
     // this warp's slot barriers (used by this warp only)
     if (lane == 0) {
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     auto load_batch = [&](int bi, int4 &d, int &e1) {
         const int k = (bi << 5) + lane;
         if (k < nk) {
-            const int t = ta + warp + k * W;
+            const int t = wa + k;
             const TileMeta a = p.meta[t];
             const TileMeta b = p.meta[t + 1];
             d = make_int4(a.nzb, a.e_begin, a.flags, b.nzb);
@@ -160,7 +169,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         xwindow(d.y, e1, xbase, nxc);
         int e0 = kb0, cnt = ncov;
         if (lane == 2) {
-            e0 = (ta + warp + k * W) * p.mwp;
+            e0 = (wa + k) * p.mwp;
             cnt = p.mwp;
         } else if (lane >= 3) {
             e0 = xbase;
@@ -208,6 +217,15 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     }
     __syncthreads();
 
+    // running sum of the open segment (SEGDOT): compensated (hi + lo) in the accumulation
+    // type, carried from one of this warp's tiles into the next while the segment runs on
+    AT chi[KB], clo[KB];
+#pragma unroll
+    for (int b = 0; b < KB; ++b) {
+        chi[b] = AT(0);
+        clo[b] = AT(0);
+    }
+
     int s = 0;        // slot of tile k
     uint32_t ph = 0;  // phase parity of that slot's barrier
     for (int k = 0; k < nk; ++k) {
@@ -233,10 +251,12 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
             if (lane == 0) atomicOr(p.err, ERR_STRUCT);
         } else {
             {
-                const int t = ta + warp + k * W;
                 const int i0 = d.y, i1 = d1.x;
-                const bool needLeft = (d.z & 1) != 0;
-                const bool needRight = (d.z & 2) != 0;
+                // the tile's first segment started in the previous warp (left record), its
+                // last continues in the next warp (right record): tile flags at the ends of
+                // this warp's range only
+                const bool needLeft = k == 0 && (d.z & 1) != 0;
+                const bool needRight = k == nk - 1 && (d.z & 2) != 0;
                 const bool dup = (d.z & 4) != 0;
                 const int xbase = d1.y;
                 const bool win = d1.z <= p.x_cap;
@@ -250,20 +270,13 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 const uint32_t mw = lane < p.mwp ? mask_s[lane] : 0u;
                 bool idx_bad = false;  // an index outside the short vector was met in this tile
 
-                // running sum of the open segment: compensated (hi + lo) in the accumulation type
-                AT chi[KB], clo[KB];
-#pragma unroll
-                for (int b = 0; b < KB; ++b) {
-                    chi[b] = AT(0);
-                    clo[b] = AT(0);
-                }
                 // Emit the finished dot product of segment `col` for vector b (SEGDOT):
-                // the tile's first segment, when it started in the previous tile, goes
-                // to the tile's left carry record (Sec. IV-A), the rest to out.
+                // the first segment of the warp's range, when it started in the previous
+                // warp, goes to the warp's left carry record (Sec. IV-A), the rest to out.
                 using AT2 = typename Pair<AT>::type;
                 auto emit = [&](int col, int b, AT value) {
                     if (needLeft && col == i0)
-                        static_cast<AT2 *>(p.rec_left)[(size_t)b * p.ntiles + t] = make_pair2(value, AT(0));
+                        static_cast<AT2 *>(p.rec_left)[(size_t)b * p.nproc + proc] = make_pair2(value, AT(0));
                     else
                         static_cast<XT *>(p.vout[b])[col] = static_cast<XT>(value);
                 };
@@ -647,7 +660,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     else
                         run_segdot8(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
                     // a segment whose end event lies in this tile is complete; the open one
-                    // continues in the next tile: right carry record
+                    // continues in this warp's next tile (kept in chi, clo) or, at the end of
+                    // the warp's range, in the next warp: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
                     if (lane == 0) {
                         for (int b = 0; b < kb; ++b) {
@@ -655,7 +669,14 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             if (col_last < i1)
                                 emit(col_last, b, v);
                             else if (needRight)
-                                static_cast<AT2 *>(p.rec_right)[(size_t)b * p.ntiles + t] = make_pair2(chi[b], clo[b]);
+                                static_cast<AT2 *>(p.rec_right)[(size_t)b * p.nproc + proc] = make_pair2(chi[b], clo[b]);
+                        }
+                    }
+                    if (col_last < i1) {
+#pragma unroll
+                        for (int b = 0; b < KB; ++b) {
+                            chi[b] = AT(0);
+                            clo[b] = AT(0);
                         }
                     }
                 } else if constexpr (MODE == MODE_SCATTER) {
