@@ -514,7 +514,8 @@ def run_ours(args):
     A = synth.wide_fp32_large(1, device=dev, scale=args.scale)  # every rank holds its own replica
     m, n, nnz = A.m, A.n, A.nnz
     order = 0 if args.stored_order else pkg.SPMV_PLAN_BANK_ORDER
-    plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order, warps_per_cta=args.warps,
+    blocks = 0 if args.atomic_scatter else pkg.SPMV_PLAN_ROW_BLOCKS
+    plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order | blocks, warps_per_cta=args.warps,
                     tile_items=args.tile_items, stages=args.stages)
     info = plan.info()
     g = torch.Generator(device=dev)
@@ -568,16 +569,19 @@ def run_ours(args):
     pkg.spmv_profile_enable(plan.handle, False)
     plan.check()
     ms_profiled = ev2.elapsed_time(ev3)
-    kt = {k: pkg.spmv_profile_read(plan.handle, k) for k in range(5)}
+    kt = {k: pkg.spmv_profile_read(plan.handle, k) for k in range(7)}
+    launches = sum(kt[k][1] for k in kt)  # every kernel launch of the K profiled steps (the same as the timed ones)
     ms_max = max_over_ranks(ms, world, dev)
     b_spmv, b_spvtm = pair_bytes(m, n, nnz)
     value = whole_job_gbs(b_spmv + b_spvtm, args.steps, world, ms_max)
 
-    # roofline of the dominant kernel (chunk scatter = SpMV local, chunk dot = SpVTM local)
+    # roofline of the dominant kernel (SpMV local: chunk scatter, or the row-block dot over the
+    # row-sorted copy; SpVTM local: chunk dot); algorithmic bytes of the method's data
     peak, peak_src = load_peaks()
     k_scatter = (nnz * 8 + (n + 1) * 4 + n * 4)  # idx + values + pointers + x
     k_segdot = (nnz * 8 + (n + 1) * 4 + m * 4 + n * 4)  # idx + values + pointers + v + u
-    cand = {"chunk_scatter": (kt[0], k_scatter), "chunk_segdot": (kt[2], k_segdot)}
+    cand = {"chunk_scatter": (kt[0], k_scatter), "chunk_segdot": (kt[2], k_segdot),
+            "row_block_dot": (kt[5], k_scatter)}
     dom = max(cand, key=lambda k: cand[k][0][0])
     (kms, kl), kbytes = cand[dom]
     avg_s = kms / max(kl, 1) / 1e3
@@ -630,13 +634,18 @@ def run_ours(args):
         tc = time.perf_counter() - tc0
         extras["cgls"] = {"iterations": it, "ms_per_iteration": round(tc * 1e3 / max(it, 1), 4),
                           "rel_grad": rel, "note": "wall clock of the call, including its setup"}
-        # the same matrix multiplied in the caller's stored order (no plan-owned copy)
+        # the same matrix multiplied in the caller's stored order (no bank-ordered copy)
         if order:
-            ps = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc")
+            ps = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=blocks)
             extras["stored_order"] = time_pair_gbs(pkg, ps, m, n, nnz, "csc", max(20, args.steps // 5))
             ps.close()
+        # SpMV by shared-memory atomic accumulation (no row-sorted copy)
+        if blocks:
+            pa = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order)
+            extras["atomic_scatter"] = time_pair_gbs(pkg, pa, m, n, nnz, "csc", max(20, args.steps // 5))
+            pa.close()
         vb = A.vals.to(torch.bfloat16)
-        pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32, flags=order)
+        pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32, flags=order | blocks)
         extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),
                                      workload=WORKLOAD.replace("fp32", "bf16values"))
         pb.close()
@@ -645,8 +654,8 @@ def run_ours(args):
         cpu = None
         if not args.skip_cpu_baseline and world == 1:
             cpu = cpu_baseline(A, target_s=args.cpu_seconds)
-        spmv_ms = (kt[0][0] + kt[1][0]) / max(kt[0][1], 1)
-        spvtm_ms = (kt[2][0] + kt[3][0]) / max(kt[2][1], 1)
+        spmv_ms = (kt[0][0] + kt[1][0] + kt[5][0] + kt[6][0]) / args.steps
+        spvtm_ms = (kt[2][0] + kt[3][0]) / args.steps
         out = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -657,23 +666,27 @@ def run_ours(args):
                           "warps_per_cta": info["warps_per_cta"], "tile_items": info["tile_items"],
                           "stages": info["stages"], "zones": info["zones"],
                           "nonzero_order": "stored" if args.stored_order else
-                          "bank order (plan-owned copy, permuted within each column)"},
+                          "bank order (plan-owned copy, permuted within each column)",
+                          "spmv_local": (f"row-sorted blocks ({info['row_blocks']} blocks, widest window "
+                                         f"{info['row_block_window']} columns)") if info["row_blocks"] else
+                          "shared-memory atomic accumulation"},
                "gflops": round(2 * 2 * nnz * args.steps * world / (ms_max / 1e3) / 1e9, 1),
                "frac_of_hbm_peak": round(value / world / peak, 4),
                "ops": {"spmv_gbs": round(b_spmv / (spmv_ms / 1e3) / 1e9, 1),
                        "spvtm_gbs": round(b_spvtm / (spvtm_ms / 1e3) / 1e9, 1),
                        "kernel_ms": {name: round(kt[k][0] / max(kt[k][1], 1), 4) for k, name in
-                                     enumerate(["chunk_scatter", "combine", "chunk_segdot", "zone_fixup", "dvalues"])
+                                     enumerate(["chunk_scatter", "combine", "chunk_segdot", "zone_fixup", "dvalues",
+                                                "row_block_dot", "row_block_fixup"])
                                      if kt[k][1]}},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "extras": extras,
-               "gpu_launches": args.steps * (4 if info["zones"] > 0 else 3),
+               "gpu_launches": launches,
                "clocks": clocks}
     plan.close()
     if extras is not None:
         del A, x, v, y, u
         torch.cuda.empty_cache()
         T = synth.tall_fp32_large(2, device=dev)
-        pt = pkg.Plan(T.m, T.n, T.ptr, T.idx, T.vals, layout="csr", flags=order)
+        pt = pkg.Plan(T.m, T.n, T.ptr, T.idx, T.vals, layout="csr", flags=order | blocks)
         extras["tall_csr"] = dict(time_pair_gbs(pkg, pt, T.m, T.n, T.nnz, "csr", max(20, args.steps // 5)),
                                   workload=f"tall_csr_m{T.m}_n{T.n}_fp32_powerlaw2.2_20dense", nnz=T.nnz)
         pt.close()
@@ -707,6 +720,8 @@ def main(argv=None):
     ap.add_argument("--stages", type=int, default=0, help="staging buffers per warp; 0 = library default")
     ap.add_argument("--stored-order", action="store_true",
                     help="multiply in the stored nonzero order (no bank-ordered plan copy)")
+    ap.add_argument("--atomic-scatter", action="store_true",
+                    help="SpMV by shared-memory atomic accumulation (no row-sorted plan copy)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

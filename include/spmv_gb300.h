@@ -89,6 +89,20 @@ typedef struct spmv_plan_s *spmv_plan_t;
                                        scratch during spmv_plan; idx and vals are not read after spmv_plan
                                        returns; results equal the stored order's up to the order of rounding;
                                        spmv_dvalues answers SPMV_ERR_UNSUPPORTED (its g would be permuted). */
+#define SPMV_PLAN_ROW_BLOCKS 0x20u   /* keep a second plan-owned copy of the nonzeros for the product that
+                                       accumulates into the short vector (y = A x of a wide CSC matrix,
+                                       u^T = v^T A of a tall CSR one): the nonzeros are cut into blocks of
+                                       whole tiles (a multiple of the SM count, one per CTA) and sorted inside
+                                       each block by their short-vector index, so that product runs as
+                                       segmented dot products over each block's window of the long vector in
+                                       shared memory, without atomics and bitwise reproducibly, and the
+                                       per-block vectors are added in FP64 in block order.  Costs
+                                       nnz x (4 + value size) bytes plus (blocks x short length) vector
+                                       entries for the plan's life and about nnz x 36 bytes of scratch
+                                       during spmv_plan.  Ignored (spmv_plan_info: row_blocks = 0) when the
+                                       plan skips validation, when the windows would not fit in shared
+                                       memory, or when the blocks would hold fewer than 8 nonzeros per
+                                       short-vector entry. */
 #define SPMV_PLAN_COO_UNSORTED 0x10u /* spmv_plan_coo only: the triples may come in any order; the plan sorts
                                        them on the device by (major, minor) index, stably (duplicates keep
                                        their input order), into its own copy of the minor indices and values
@@ -122,6 +136,8 @@ typedef struct {
     double imbalance;          /* Delta = P (max - min) / Z (Sec. VI), 0 when Z = 0 */
     int64_t workspace_bytes;   /* device bytes owned by the plan */
     double setup_ms;           /* device time of the set-up kernels */
+    int32_t row_blocks;        /* blocks of the row-sorted copy (SPMV_PLAN_ROW_BLOCKS), 0 if none */
+    int32_t row_block_window;  /* widest window of the long vector a block reads (elements) */
 } spmv_plan_info_t;
 
 /* Per-chunk set-up values (spmv_plan_chunks), one per chunk p_c (Sec. IV-B, Table III). */
@@ -240,7 +256,8 @@ spmv_status spmv_check(spmv_plan_t plan, void *stream);
 
 /* Kernel timers of a plan created with SPMV_PLAN_PROFILE (or switched on with
  * spmv_profile_enable).  kernel: 0 = chunk scatter (SpMV local), 1 = partial
- * combine, 2 = chunk dot (SpVTM local), 3 = zone fixup, 4 = dvalues.
+ * combine, 2 = chunk dot (SpVTM local), 3 = zone fixup, 4 = dvalues,
+ * 5 = row-block dot (the SpMV local step over the row-sorted copy), 6 = its zone fixup.
  * Synchronizes the device.  *ms = summed event time, *launches = number of
  * timed launches.  Timing brackets every launch with two events, which waits
  * for each kernel to drain before the next starts: a profiled sequence of

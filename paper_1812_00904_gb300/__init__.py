@@ -13,7 +13,7 @@ import ctypes
 from . import _lib
 from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, SPMV_F64, SPMV_OP_AX, SPMV_OP_VTA,
                    SPMV_PLAN_BANK_ORDER, SPMV_PLAN_COO_UNSORTED, SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE,
-                   SPMV_PLAN_SHORT_IN_GLOBAL, SpmvError)
+                   SPMV_PLAN_ROW_BLOCKS, SPMV_PLAN_SHORT_IN_GLOBAL, SpmvError)
 
 __all__ = [
     "spmv_plan", "spmv_plan_ex", "spmv_plan_coo", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
@@ -22,7 +22,7 @@ __all__ = [
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
     "SPMV_CSC_WIDE", "SPMV_CSR_TALL", "SPMV_F64", "SPMV_F32", "SPMV_BF16", "SPMV_F16", "SPMV_OP_AX", "SPMV_OP_VTA",
     "SPMV_PLAN_NO_VALIDATE", "SPMV_PLAN_PROFILE", "SPMV_PLAN_SHORT_IN_GLOBAL", "SPMV_PLAN_BANK_ORDER",
-    "SPMV_PLAN_COO_UNSORTED",
+    "SPMV_PLAN_COO_UNSORTED", "SPMV_PLAN_ROW_BLOCKS",
 ]
 
 

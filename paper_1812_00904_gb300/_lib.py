@@ -24,8 +24,10 @@ SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_F16 = 0, 1, 2, 3
 SPMV_OP_AX, SPMV_OP_VTA = 0, 1
 SPMV_PLAN_NO_VALIDATE, SPMV_PLAN_PROFILE, SPMV_PLAN_SHORT_IN_GLOBAL, SPMV_PLAN_BANK_ORDER = 0x1, 0x2, 0x4, 0x8
 SPMV_PLAN_COO_UNSORTED = 0x10
+SPMV_PLAN_ROW_BLOCKS = 0x20
 
 KERNEL_SCATTER, KERNEL_COMBINE, KERNEL_SEGDOT, KERNEL_FIXUP, KERNEL_DVALUES = 0, 1, 2, 3, 4
+KERNEL_ROWBLOCK_DOT, KERNEL_ROWBLOCK_FIXUP = 5, 6
 
 
 class SpmvError(RuntimeError):
@@ -46,7 +48,8 @@ class spmv_plan_info_t(ctypes.Structure):
                 ("tile_items", ctypes.c_int32), ("stages", ctypes.c_int32), ("tiles", ctypes.c_int32),
                 ("zones", ctypes.c_int32), ("max_zone_size", ctypes.c_int32), ("short_on_chip", ctypes.c_int32),
                 ("batch_width", ctypes.c_int32), ("max_chunk_nnz", ctypes.c_int64), ("min_chunk_nnz", ctypes.c_int64),
-                ("imbalance", ctypes.c_double), ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double)]
+                ("imbalance", ctypes.c_double), ("workspace_bytes", ctypes.c_int64), ("setup_ms", ctypes.c_double),
+                ("row_blocks", ctypes.c_int32), ("row_block_window", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -69,7 +69,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(BUILD, os.path.basename(s) + ".o") for s in srcs]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread", "-Xlinker", "--no-undefined"],
+                           capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, LIB)

@@ -54,6 +54,11 @@ cudaError_t launch_stream(const spmv_plan_s *p, int mode, int kb, const LaunchAr
 int kb_template(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : 8; }
 int kb_log2(int kbt) { return kbt <= 1 ? 0 : kbt <= 2 ? 1 : kbt <= 4 ? 2 : 3; }
 
+// Tiles per chunk of the streaming kernels' full rounds: a warp carries a segment across the
+// tiles of a chunk in registers, so overlap zones (and their FP64 fix-up) arise only at chunk
+// boundaries, while the CTA's warps still stream a compact stretch of the arrays.
+constexpr int CHUNK_TILES = 8;
+
 // Kernel timers: bracket one launch with events when the plan profiles.
 struct ProfScope {
     spmv_plan_s *p;
@@ -95,6 +100,8 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.checked = (p->flags & SPMV_PLAN_NO_VALIDATE) ? 1 : 0;
     sp.rec_left = p->rec_left;
     sp.rec_right = p->rec_right;
+    sp.chunk_tiles = p->chunk_tiles;
+    sp.win = p->win;
     sp.err = p->err;
     return sp;
 }
@@ -171,7 +178,9 @@ spmv_status set_error(spmv_status st, const std::string &msg) {
 }
 
 size_t plan_footprint(const spmv_plan_s *p) {
-    return p->ws_bytes + p->owned_bytes + (size_t)p->nnz * (4 + p->sv) + (size_t)(p->n_major + 1) * 4;
+    size_t b = p->ws_bytes + p->owned_bytes + (size_t)p->nnz * (4 + p->sv) + (size_t)(p->n_major + 1) * 4;
+    if (p->tplan) b += p->tplan->ws_bytes + p->tplan->owned_bytes + p->bws_bytes + p->bown_bytes;
+    return b;
 }
 
 spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
@@ -208,7 +217,10 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     return SPMV_OK;
 }
 
-spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
+// The segmented pass (and its zone fix-up) of plan p; the launches are timed as kernels
+// id_dot / id_fix of plan `prof`.
+static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
+                                   spmv_plan_s *prof, int id_dot, int id_fix) {
     const size_t out_bytes = (size_t)p->n_major * p->sx;
     if (p->nnz == 0 || p->n_minor == 0) {
         if (out_bytes)
@@ -217,7 +229,7 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
     }
     if (!p->onchip && kb > 1) {
         for (int b = 0; b < kb; ++b) {
-            spmv_status st = run_segdot(p, 1, in + b, out + b, s);
+            spmv_status st = run_segdot_impl(p, 1, in + b, out + b, s, prof, id_dot, id_fix);
             if (st != SPMV_OK) return st;
         }
         return SPMV_OK;
@@ -235,12 +247,33 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
     a.sp.nproc = pz.nproc;
     a.stream = s;
     {
-        ProfScope ps(p, 2, s);
+        ProfScope ps(prof, id_dot, s);
         CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
     }
     if (pz.z > 0) {
-        ProfScope ps(p, 3, s);
+        ProfScope ps(prof, id_fix, s);
         CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, pz.zones, pz.z, p->rec_left, p->rec_right, pz.nproc, kb, out, s));
+    }
+    return SPMV_OK;
+}
+
+spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
+    return run_segdot_impl(p, kb, in, out, s, p, 2, 3);
+}
+
+// The short-vector product over the row-sorted blocks (SPMV_PLAN_ROW_BLOCKS): the sub-plan's
+// windowed segmented pass writes every block's short vector into ypart (its fix-up completes
+// the entries split between chunks), then the blocks' vectors are added in FP64 in block
+// order (Sec. III step 2).  One vector at a time: a window of several would not fit on chip.
+static spmv_status run_row_blocks(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
+    spmv_plan_s *q = p->tplan;
+    const bool f64 = p->vec_t == SPMV_F64;
+    for (int b = 0; b < kb; ++b) {
+        void *yp = p->ypart;
+        spmv_status st = run_segdot_impl(q, 1, in + b, &yp, s, p, 5, 6);
+        if (st != SPMV_OK) return st;
+        ProfScope ps(p, 1, s);
+        CUDA_TRY(launch_combine(f64, f64, p->ypart, p->blocks, p->n_minor, 1, out + b, s));
     }
     return SPMV_OK;
 }
@@ -264,6 +297,7 @@ static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, voi
 
 spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *const *out, cudaStream_t s) {
     const bool scatter = (op == SPMV_OP_AX) == (p->layout == SPMV_CSC_WIDE);
+    if (scatter && p->tplan && p->nnz > 0) return run_row_blocks(p, k, in, out, s);
     for (int g0 = 0; g0 < k; g0 += p->batch_width) {
         const int kb = std::min(p->batch_width, k - g0);
         spmv_status st = scatter ? run_scatter(p, kb, in + g0, out + g0, s) : run_segdot(p, kb, in + g0, out + g0, s);
@@ -274,10 +308,13 @@ spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *c
 
 }  // namespace gbk
 
-namespace {
+namespace gbk {
 
-void free_plan(spmv_plan_s *p) {
+void plan_free(spmv_plan_s *p) {
     if (!p) return;
+    plan_free(p->tplan);
+    if (p->bws) cudaFree(p->bws);
+    if (p->bown) cudaFree(p->bown);
     for (auto &pr : p->prof) {
         cudaEventDestroy(pr.a);
         cudaEventDestroy(pr.b);
@@ -293,9 +330,13 @@ void free_plan(spmv_plan_s *p) {
     delete p;
 }
 
+}  // namespace gbk
+
+namespace {
+
 struct PlanGuard {
     spmv_plan_s *p;
-    ~PlanGuard() { free_plan(p); }
+    ~PlanGuard() { plan_free(p); }
 };
 
 // Runs `fn` on device pointers, staging host pointers through plan buffers.
@@ -349,6 +390,15 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
                          const int32_t *idx, const void *vals, int32_t val_dtype, int32_t vec_dtype, void *stream,
                          uint32_t flags, const spmv_plan_opts *opts) {
     g_last_error.clear();
+    return plan_create(out, m, n, nnz, layout, ptr, idx, vals, val_dtype, vec_dtype, static_cast<cudaStream_t>(stream),
+                       flags, opts, nullptr);
+}
+
+}  // extern "C"
+
+spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nnz, int32_t layout, const int32_t *ptr,
+                             const int32_t *idx, const void *vals, int32_t val_dtype, int32_t vec_dtype,
+                             cudaStream_t s, uint32_t flags, const spmv_plan_opts *opts, const PlanInternal *pi) {
     if (!out) return set_error(SPMV_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (layout != SPMV_CSC_WIDE && layout != SPMV_CSR_TALL) return set_error(SPMV_ERR_INVALID_ARG, "bad layout");
@@ -368,8 +418,6 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         if (q && classify(q) != PK_DEVICE)
             return set_error(SPMV_ERR_INVALID_ARG, "ptr, idx and vals must be device pointers");
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-
     spmv_plan_s *p = new (std::nothrow) spmv_plan_s();
     if (!p) return set_error(SPMV_ERR_OOM, "host allocation failed");
     PlanGuard guard{p};
@@ -423,7 +471,7 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
         if (warps_for(p, mode, 1) < 1) return set_error(SPMV_ERR_INVALID_ARG, "tile_items/stages leave no room for one warp");
     // vectors per pass of spmv_batch: as many as still leave most of the warps
     p->batch_width = 1;
-    if (p->onchip) {
+    if (p->onchip && !(pi && pi->segdot_only)) {
         const int want = std::min(warps_for(p, MODE_SCATTER, 1), 12);
         for (int kb : {8, 4, 2}) {
             if (warps_for(p, MODE_SCATTER, kb) >= want && warps_for(p, MODE_SEGDOT, kb) >= want) {
@@ -519,7 +567,8 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
 
     // ---- workspace, part 2: tiles (descriptors, masks), processor zones, records and partial sums
     const int nt = p->ntiles;
-    p->ctas = std::max(1, std::min(sms, nt));
+    p->ctas = (pi && pi->ctas > 0) ? std::min(pi->ctas, std::max(nt, 1)) : std::max(1, std::min(sms, nt));
+    p->chunk_tiles = CHUNK_TILES;
     // processors (warps holding tiles) of the segmented passes, per vector-slot template in use
     const int ntpl = p->onchip ? kb_log2(kb_template(p->batch_width)) + 1 : 1;
     std::vector<std::vector<int32_t>> pnzb(ntpl);
@@ -527,13 +576,14 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     for (int i = 0; i < ntpl; ++i) {
         spmv_plan_s::ProcZones &pz = p->pz[i];
         pz.W = std::max(1, warps_for(p, MODE_SEGDOT, 1 << i));
-        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, nullptr);
+        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, p->chunk_tiles, nullptr);
         pnzb[i].resize((size_t)pz.nproc + 1);
-        stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, pnzb[i].data());
+        stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, p->chunk_tiles, pnzb[i].data());
         p->max_nproc = std::max(p->max_nproc, pz.nproc);
     }
-    const size_t part_bytes = p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
-                                        : (size_t)p->n_minor * sizeof(double);
+    const size_t part_bytes = (pi && pi->segdot_only) ? 16
+                              : p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
+                                          : (size_t)p->n_minor * sizeof(double);
     const size_t rec_bytes = (size_t)p->batch_width * p->max_nproc * 2 * p->sa;
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
@@ -593,15 +643,22 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->setup_ms = ms;
+    // the row-sorted copy for the short-vector accumulating product (validated plans only)
+    if (!pi && (flags & SPMV_PLAN_ROW_BLOCKS) && !(flags & SPMV_PLAN_NO_VALIDATE) && nnz > 0) {
+        spmv_status st = build_row_blocks(p, sms, s);
+        if (st != SPMV_OK) return st;
+    }
     guard.p = nullptr;
     *out = p;
     return SPMV_OK;
 }
 
+extern "C" {
+
 spmv_status spmv_plan_destroy(spmv_plan_t plan) {
     if (!plan) return SPMV_OK;
     cudaDeviceSynchronize();
-    free_plan(plan);
+    plan_free(plan);
     return SPMV_OK;
 }
 
@@ -629,6 +686,9 @@ spmv_status spmv_plan_info(spmv_plan_t p, spmv_plan_info_t *info) {
     info->imbalance = p->nnz > 0 ? (double)p->P * (double)(p->max_chunk - p->min_chunk) / (double)p->nnz : 0.0;
     info->workspace_bytes = (int64_t)(p->ws_bytes + p->owned_bytes);
     info->setup_ms = p->setup_ms;
+    info->row_blocks = p->tplan ? p->blocks : 0;
+    info->row_block_window = p->tplan ? p->block_window : 0;
+    if (p->tplan) info->workspace_bytes += (int64_t)(p->tplan->ws_bytes + p->tplan->owned_bytes + p->bws_bytes + p->bown_bytes);
     return SPMV_OK;
 }
 
@@ -743,8 +803,13 @@ spmv_status spmv_check(spmv_plan_t p, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaStreamSynchronize(s));
     CUDA_TRY(cudaGetLastError());
-    int32_t e = 0;
+    int32_t e = 0, et = 0;
     CUDA_TRY(cudaMemcpy(&e, p->err, 4, cudaMemcpyDeviceToHost));
+    if (p->tplan) {
+        CUDA_TRY(cudaMemcpy(&et, p->tplan->err, 4, cudaMemcpyDeviceToHost));
+        if (et) CUDA_TRY(cudaMemset(p->tplan->err, 0, 4));
+        e |= et;
+    }
     if (e) {
         CUDA_TRY(cudaMemset(p->err, 0, 4));
         std::string msg = "device error:";
@@ -757,7 +822,7 @@ spmv_status spmv_check(spmv_plan_t p, void *stream) {
 }
 
 spmv_status spmv_profile_read(spmv_plan_t p, int32_t kernel, double *ms, int64_t *launches) {
-    if (!p || kernel < 0 || kernel > 4) return set_error(SPMV_ERR_INVALID_ARG, "bad arguments");
+    if (!p || kernel < 0 || kernel > 6) return set_error(SPMV_ERR_INVALID_ARG, "bad arguments");
     CUDA_TRY(cudaDeviceSynchronize());
     std::lock_guard<std::mutex> lk(p->prof_mu);
     for (auto &pr : p->prof) {
@@ -786,7 +851,7 @@ spmv_status spmv_profile_reset(spmv_plan_t p) {
     int64_t n;
     spmv_profile_read(p, 0, &d, &n);
     std::lock_guard<std::mutex> lk(p->prof_mu);
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 7; ++i) {
         p->prof_ms[i] = 0;
         p->prof_n[i] = 0;
     }

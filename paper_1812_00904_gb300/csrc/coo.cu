@@ -226,22 +226,17 @@ __global__ void coo_unpack_kernel(const uint64_t *__restrict__ keys, const int32
 }
 
 }  // namespace
-}  // namespace gbk
 
-using namespace gbk;
+CooSort::~CooSort() {
+    if (tmp) cudaFree(tmp);
+    if (own) cudaFree(own);
+}
 
-namespace {
-
-// Device buffers of one unsorted-triple conversion (freed together).
-struct CooSort {
-    void *tmp = nullptr;   // keys x2, payloads x2, histogram, block sums
-    void *own = nullptr;   // sorted minor indices + values (handed to the plan)
-    size_t own_bytes = 0;
-    ~CooSort() {
-        if (tmp) cudaFree(tmp);
-        if (own) cudaFree(own);
-    }
-};
+cudaError_t launch_coo_ptr(const int32_t *major_sorted, int64_t nnz, int n_major, int32_t *ptr, int grid,
+                           cudaStream_t s) {
+    coo_ptr_kernel<<<grid, 256, 0, s>>>(major_sorted, nnz, n_major, ptr);
+    return cudaGetLastError();
+}
 
 // Sorts the triples by (major, minor), stably: the sorted minor indices and values go to the
 // plan-owned block, the sorted major indices to the temporary one; all three come back through
@@ -294,6 +289,12 @@ spmv_status coo_sort(CooSort &cs, const int32_t *major, const int32_t *minor, co
     *vals_sorted = ovals;
     return SPMV_OK;
 }
+
+}  // namespace gbk
+
+using namespace gbk;
+
+namespace {
 
 int dsize(int t) { return t == SPMV_F64 ? 8 : t == SPMV_F32 ? 4 : (t == SPMV_BF16 || t == SPMV_F16) ? 2 : 0; }
 

@@ -328,23 +328,25 @@ cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles,
     return cudaGetLastError();
 }
 
-// The warps of a streaming launch that hold tiles, in the kernel's order: CTA g takes
-// tiles [ta, ta + nct) by the Sec. II rule over the grid, its warp w the same rule
-// over its W warps.  nzb[q] = first nonzero of processor q; nzb[nproc] = nnz.
-int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int32_t *nzb) {
-    if (ctas < 1 || W < 1) return 0;
+// The processors of a streaming launch with W warps per CTA, in the kernel's order:
+// CTA g takes tiles [ta, ta + nct) by the Sec. II rule over the grid; they form FR =
+// nct / (W C) rounds of W chunks of C tiles, then the L tiles left over split among the W
+// warps by the Sec. II rule (one final chunk per warp that gets a tile).
+// nzb[q] = first nonzero of chunk q; nzb[nproc] = nnz.
+int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int C, int32_t *nzb) {
+    if (ctas < 1 || W < 1 || C < 1) return 0;
     const int tq = ntiles / ctas, tr = ntiles % ctas;
     int np = 0;
+    auto put = [&](int tile) {
+        if (nzb) nzb[np] = (int)((int64_t)tile * T < nnz ? (int64_t)tile * T : nnz);
+        ++np;
+    };
     for (int g = 0; g < ctas; ++g) {
         const int ta = g * tq + (g < tr ? g : tr);
         const int nct = tq + (g < tr ? 1 : 0);
-        for (int w = 0; w < W; ++w) {
-            const int nk = nct / W + (w < nct % W ? 1 : 0);
-            if (nk == 0) continue;
-            const int wa = ta + w * (nct / W) + (w < nct % W ? w : nct % W);
-            if (nzb) nzb[np] = (int)((int64_t)wa * T < nnz ? (int64_t)wa * T : nnz);
-            ++np;
-        }
+        const int FR = nct / (W * C), L = nct - FR * W * C;
+        for (int j = 0; j < FR * W; ++j) put(ta + j * C);
+        for (int w = 0; w < W && w < L; ++w) put(ta + FR * W * C + w * (L / W) + (w < L % W ? w : L % W));
     }
     if (nzb) nzb[np] = nnz;
     return np;

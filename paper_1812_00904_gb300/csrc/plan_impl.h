@@ -27,6 +27,7 @@ struct spmv_plan_s {
     int ctas = 0, W = 0, T = 0, S = 0;  // W: most warps per CTA (each pass fits what shared memory holds)
     int W_info = 0;                       // warps of the single-vector scatter pass (spmv_plan_info)
     int mwp = 0, x_cap = 0, pptr_len = 0, smem_max = 0;  // masks words per tile, window elements per tile
+    int chunk_tiles = 1;  // tiles per chunk of the streaming kernels' full rounds
     bool onchip = false;
     int batch_width = 1;
 
@@ -42,12 +43,12 @@ struct spmv_plan_s {
     int32_t *err = nullptr;
     gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
     uint32_t *masks = nullptr;
-    // Overlap zones among the processors of the segmented passes (the warps that hold
-    // tiles, Sec. II groups of whole tiles), one table per vector-slot template of the
-    // passes (index log2 kbt: 1, 2, 4, 8 vectors), since the warp count can differ.
+    // Overlap zones among the processors of the segmented passes (chunks of whole tiles,
+    // contiguous Sec. II groups), one table per vector-slot template of the passes (index
+    // log2 kbt: 1, 2, 4, 8 vectors), since the chunks depend on the pass's warp count.
     struct ProcZones {
         int W = 0;      // warps per CTA of those passes
-        int nproc = 0;  // processors, the stride of the carry records
+        int nproc = 0;  // processors (chunks), the stride of the carry records
         int z = 0;      // overlap zones among them
         gbk::ZoneDev *zones = nullptr;
     };
@@ -67,6 +68,16 @@ struct spmv_plan_s {
     void *owned_nz = nullptr;   // plan-owned idx and vals: bank order, or triples sorted by spmv_plan_coo
     size_t owned_bytes = 0;
 
+    // row-sorted blocks (SPMV_PLAN_ROW_BLOCKS): the sub-plan over the sorted copy and its buffers
+    spmv_plan_s *tplan = nullptr;
+    int blocks = 0, block_window = 0;
+    void *bws = nullptr;        // windows, the copy's pointer array, per-block short vectors
+    size_t bws_bytes = 0;
+    void *bown = nullptr;       // the sorted copy's indices and values (when the sub-plan borrows them)
+    size_t bown_bytes = 0;
+    void *ypart = nullptr;      // per-block short vectors [block][n_minor]
+    const int2 *win = nullptr;  // sub-plan: per CTA window of the long vector
+
     // kernel timers (SPMV_PLAN_PROFILE)
     struct Prof {
         int kernel;
@@ -75,11 +86,24 @@ struct spmv_plan_s {
     std::atomic<bool> prof_on{false};  // SPMV_PLAN_PROFILE at creation; spmv_profile_enable later
     std::mutex prof_mu;
     std::vector<Prof> prof;
-    double prof_ms[5] = {0, 0, 0, 0, 0};
-    int64_t prof_n[5] = {0, 0, 0, 0, 0};
+    double prof_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t prof_n[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace gbk {
+
+// Internal overrides of a plan made by the library itself.
+struct PlanInternal {
+    int ctas = 0;             // CTAs of every pass (0: one per SM, at most one per tile)
+    bool segdot_only = false; // only single-vector segmented passes will run
+};
+spmv_status plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nnz, int32_t layout, const int32_t *ptr,
+                        const int32_t *idx, const void *vals, int32_t val_dtype, int32_t vec_dtype, cudaStream_t s,
+                        uint32_t flags, const spmv_plan_opts *opts, const PlanInternal *pi);
+void plan_free(spmv_plan_s *p);
+// Build the row-sorted block copy of a finished plan (blocks.cu); leaves the plan unchanged
+// when the copy would not pay or its windows do not fit on chip.
+spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s);
 
 // Internal entry points on device pointers (no host staging).  `in`/`out`
 // hold kb <= plan->batch_width vector pointers (kb == 1 off chip).
@@ -94,5 +118,21 @@ cudaError_t launch_bank_order(const int32_t *ptr, int n_major, int nnz, const in
                               int val_bytes, int32_t *oidx, void *ovals, int32_t *slots, int T, int banks,
                               cudaStream_t s);
 spmv_status set_error(spmv_status st, const std::string &msg);
+
+// Device buffers of one stable (major, minor) sort of coordinate triples (coo.cu; freed together).
+struct CooSort {
+    void *tmp = nullptr;   // keys x2, payloads x2, histogram, block sums
+    void *own = nullptr;   // sorted minor indices + values (handed to the plan)
+    size_t own_bytes = 0;
+    ~CooSort();
+};
+// Stable LSD radix sort of the triples by (major, minor) on `s`: sorted minor indices and values
+// in cs.own, sorted major indices in a buffer inside cs.tmp.  Range errors set bits 1 / 4 of err.
+spmv_status coo_sort(CooSort &cs, const int32_t *major, const int32_t *minor, const void *vals, int sv, int64_t nnz,
+                     int n_major, int n_minor, int grid, int32_t *err, cudaStream_t s, const int32_t **major_sorted,
+                     int32_t **minor_sorted, void **vals_sorted);
+// ptr[j] = number of entries of the sorted major-index array below j, j = 0..n_major.
+cudaError_t launch_coo_ptr(const int32_t *major_sorted, int64_t nnz, int n_major, int32_t *ptr, int grid,
+                           cudaStream_t s);
 
 }  // namespace gbk

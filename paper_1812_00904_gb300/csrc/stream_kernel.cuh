@@ -1,7 +1,11 @@
 // Streaming kernel: the nonzeros are cut into equal-count tiles of T nonzeros;
-// each CTA takes a contiguous range of tiles by the Sec. II rule, and within a
-// CTA every warp takes a contiguous sub-range by the same rule: the warps are the
-// "processors" of Sec. II (each a contiguous, equally sized group of nonzeros).
+// each CTA takes a contiguous range of tiles by the Sec. II rule and cuts it into
+// chunks: rounds of W chunks of C consecutive tiles, warp w taking chunk w of every
+// round (so the CTA's warps stream neighbouring parts of the arrays at any time),
+// then the tiles left over split among the W warps by the Sec. II rule, one final
+// chunk each.  Every warp gets the same number of tiles, give or take one.  The
+// chunks are the "processors" of Sec. II: contiguous groups of nonzeros, each
+// owning its own overlap-zone records.
 // Every warp streams its own tiles through S shared-memory slots of its own:
 // when it has finished a tile it issues the bulk (TMA) copies of the tile S
 // ahead into the freed slot (one copy per array: indices, values, segment-start
@@ -19,11 +23,11 @@
 //                 an on-chip copy of the short vector per CTA.
 //   MODE_SEGDOT:  out[j] = sum_k val[k] * w[idx[k]] over segment j -- v^T A_(i)
 //                 of Sec. IV-A (wide CSC u^T = v^T A; tall CSR y = A x).  A
-//                 segment that runs on from one of a warp's tiles into the next
-//                 is carried in registers; the first and last segments of a
-//                 warp's range that continue in the neighbouring warps (overlap
-//                 zones) leave their partial sums in the warp's carry records
-//                 for the zone fixup.
+//                 segment that runs on from one tile of a chunk into the next is
+//                 carried in registers; the first and last segments of a chunk
+//                 that continue in the neighbouring chunks (overlap zones) leave
+//                 their partial sums in the chunk's carry records for the zone
+//                 fixup.
 //   MODE_DVALUES: g[k] = minor[idx[k]] * major[seg(k)].
 #pragma once
 
@@ -76,18 +80,26 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
     unsigned char *myslots = smem + p.vec_region_bytes + BAR_BYTES + (size_t)warp * S * p.slot_bytes;
 
-    // this CTA's tiles: the Sec. II rule over the grid; this warp's: the same rule over the
-    // CTA's W warps, tiles wa .. wa + nk - 1
+    // this CTA's tiles [ta, ta + nct): the Sec. II rule over the grid; FR full rounds of W
+    // chunks of C tiles, then the L tiles left, one final chunk per warp
     const int G = gridDim.x, g = blockIdx.x;
     const int tq = p.ntiles / G, tr = p.ntiles % G;
     const int ta = g * tq + min(g, tr);
     const int nct = tq + (g < tr ? 1 : 0);
-    const int wa = ta + warp * (nct / W) + min(warp, nct % W);
-    const int nk = nct / W + (warp < nct % W ? 1 : 0);
-    // processor number of this warp among the warps that hold tiles (the index of its
-    // carry records): all W warps of every CTA when every CTA has at least W tiles,
-    // else one tile per warp, numbered like the tiles
-    const int proc = (tq >= W) ? g * W + warp : wa;
+    const int C = p.chunk_tiles;
+    const int FR = nct / (W * C);
+    const int L = nct - FR * W * C;
+    const int fbase = ta + FR * W * C + warp * (L / W) + min(warp, L % W);  // this warp's final chunk
+    const int nk = FR * C + L / W + (warp < L % W ? 1 : 0);                // tiles of this warp
+    auto tile_of = [&](int k) {  // tile of this warp's k-th tile
+        return k < FR * C ? ta + ((k / C) * W + warp) * C + k % C : fbase + (k - FR * C);
+    };
+    // processors (chunks) before this CTA: a CTA of n tiles has FR(n) W + min(W, L(n)) chunks
+    auto chunks_of = [&](int n) {
+        const int fr = n / (W * C);
+        return fr * W + min(W, n - fr * W * C);
+    };
+    const int chunk0 = g * chunks_of(tq) + min(g, tr) * (chunks_of(tq + 1) - chunks_of(tq));
 
     // this warp's slot barriers (used by this warp only)
     if (lane == 0) {
@@ -102,7 +114,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     auto load_batch = [&](int bi, int4 &d, int &e1) {
         const int k = (bi << 5) + lane;
         if (k < nk) {
-            const int t = wa + k;
+            const int t = tile_of(k);
             const TileMeta a = p.meta[t];
             const TileMeta b = p.meta[t + 1];
             d = make_int4(a.nzb, a.e_begin, a.flags, b.nzb);
@@ -169,7 +181,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         xwindow(d.y, e1, xbase, nxc);
         int e0 = kb0, cnt = ncov;
         if (lane == 2) {
-            e0 = (wa + k) * p.mwp;
+            e0 = tile_of(k) * p.mwp;
             cnt = p.mwp;
         } else if (lane >= 3) {
             e0 = xbase;
@@ -207,15 +219,29 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
             AT *acc = reinterpret_cast<AT *>(smem);
             for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
         } else {
+            // the input vector, or this CTA's window of it (row-sorted blocks)
             XT *vs = reinterpret_cast<XT *>(smem);
-            for (int i = threadIdx.x; i < p.n_minor; i += blockDim.x) {
+            int wb = 0, wl = p.n_minor;
+            if (MODE == MODE_SEGDOT && p.win) {
+                const int2 w = p.win[blockIdx.x];
+                wb = w.x;
+                wl = min(w.y, p.n_minor);
+            }
+            for (int i = threadIdx.x; i < wl; i += blockDim.x) {
 #pragma unroll
                 for (int b = 0; b < KB; ++b)
-                    vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[i] : zero_of<XT>();
+                    vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[wb + i] : zero_of<XT>();
             }
         }
     }
     __syncthreads();
+
+    // the open segment at the start of the current chunk: its first segment, and whether that
+    // began in the previous chunk (then its sum goes to the chunk's left record)
+    int cfirst = -1;
+    bool cleft = false;
+    // first element of this CTA's window of the input vector (SEGDOT over row-sorted blocks)
+    const int vwin = (MODE == MODE_SEGDOT && p.win) ? p.win[blockIdx.x].x : 0;
 
     // running sum of the open segment (SEGDOT): compensated (hi + lo) in the accumulation
     // type, carried from one of this warp's tiles into the next while the segment runs on
@@ -252,11 +278,18 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         } else {
             {
                 const int i0 = d.y, i1 = d1.x;
-                // the tile's first segment started in the previous warp (left record), its
-                // last continues in the next warp (right record): tile flags at the ends of
-                // this warp's range only
-                const bool needLeft = k == 0 && (d.z & 1) != 0;
-                const bool needRight = k == nk - 1 && (d.z & 2) != 0;
+                // position of the tile in its chunk; the chunk's first segment started in the
+                // previous chunk (left record) and its last continues in the next (right record)
+                // by the flags of the chunk's first and last tiles
+                const bool in_round = k < FR * C;
+                const bool chunk_first = in_round ? (k % C) == 0 : k == FR * C;
+                const bool chunk_last = in_round ? (k % C) == C - 1 : k == nk - 1;
+                const int proc = chunk0 + (in_round ? (k / C) * W : FR * W) + warp;
+                if (chunk_first) {
+                    cfirst = i0;
+                    cleft = (d.z & 1) != 0;
+                }
+                const bool needRight = chunk_last && (d.z & 2) != 0;
                 const bool dup = (d.z & 4) != 0;
                 const int xbase = d1.y;
                 const bool win = d1.z <= p.x_cap;
@@ -271,11 +304,11 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 bool idx_bad = false;  // an index outside the short vector was met in this tile
 
                 // Emit the finished dot product of segment `col` for vector b (SEGDOT):
-                // the first segment of the warp's range, when it started in the previous
-                // warp, goes to the warp's left carry record (Sec. IV-A), the rest to out.
+                // the chunk's first segment, when it started in the previous chunk, goes
+                // to the chunk's left carry record (Sec. IV-A), the rest to out.
                 using AT2 = typename Pair<AT>::type;
                 auto emit = [&](int col, int b, AT value) {
-                    if (needLeft && col == i0)
+                    if (cleft && col == cfirst)
                         static_cast<AT2 *>(p.rec_left)[(size_t)b * p.nproc + proc] = make_pair2(value, AT(0));
                     else
                         static_cast<XT *>(p.vout[b])[col] = static_cast<XT>(value);
@@ -554,7 +587,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                 if constexpr (SMEMV) {
                                     w_ = static_cast<AT>(reinterpret_cast<const XT *>(smem)[ix[e] * KB + b]);
                                 } else {
-                                    w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + ix[e]));
+                                    w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + vwin + ix[e]));
                                 }
                             }
                             pr[e] = va[e] * w_;
@@ -660,8 +693,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     else
                         run_segdot8(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
                     // a segment whose end event lies in this tile is complete; the open one
-                    // continues in this warp's next tile (kept in chi, clo) or, at the end of
-                    // the warp's range, in the next warp: right carry record
+                    // continues in the chunk's next tile (kept in chi, clo) or, at the end of
+                    // the chunk, in the next chunk: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
                     if (lane == 0) {
                         for (int b = 0; b < kb; ++b) {
@@ -672,7 +705,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                 static_cast<AT2 *>(p.rec_right)[(size_t)b * p.nproc + proc] = make_pair2(chi[b], clo[b]);
                         }
                     }
-                    if (col_last < i1) {
+                    if (col_last < i1 || chunk_last) {  // nothing runs on into this warp's next tile
 #pragma unroll
                         for (int b = 0; b < KB; ++b) {
                             chi[b] = AT(0);

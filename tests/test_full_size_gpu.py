@@ -24,9 +24,13 @@ def _host(A, vals_dtype=None):
                               v.double().cpu().numpy()), v
 
 
-def _check(A, val_dtype, what):
+# the benchmark's plans: bank-ordered nonzeros and the row-sorted copy for the short-vector product
+BENCH_FLAGS = pkg.SPMV_PLAN_BANK_ORDER | pkg.SPMV_PLAN_ROW_BLOCKS
+
+
+def _check(A, val_dtype, what, flags=BENCH_FLAGS):
     stored, vals = _host(A, val_dtype)
-    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, vals, layout=A.layout, vec_dtype=torch.float32)
+    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, vals, layout=A.layout, vec_dtype=torch.float32, flags=flags)
     g = torch.Generator(device=DEV)
     g.manual_seed(11)
     x = torch.rand(A.n, generator=g, device=DEV) * 2 - 1
@@ -51,6 +55,14 @@ def test_wide_fp32_full_size():
     A = synth.wide_fp32_large(1, device=DEV)
     _, info = _check(A, None, "wide fp32")
     assert info["tile_items"] == 512 and info["stages"] == 2  # the benchmark's configuration
+    assert info["row_blocks"] > 0
+
+
+def test_wide_fp32_full_size_atomic_path():
+    """The same matrix without the copies: SpMV by shared-memory atomic accumulation."""
+    A = synth.wide_fp32_large(1, device=DEV)
+    _, info = _check(A, None, "wide fp32 atomic", flags=0)
+    assert info["row_blocks"] == 0
 
 
 def test_wide_bf16_values_full_size():
@@ -65,15 +77,16 @@ def test_wide_bf16_values_full_size():
 
 def test_tall_fp32_full_size():
     A = synth.tall_fp32_large(2, device=DEV)
-    _check(A, None, "tall fp32")
+    _, info = _check(A, None, "tall fp32")
+    assert info["row_blocks"] > 0
 
 
 def test_wide_fp32_full_size_through_pinned_host_vectors():
-    """The end-to-end configuration of the benchmark: a bank-ordered plan and pinned host
+    """The end-to-end configuration of the benchmark: the benchmark's plan and pinned host
     vectors staged by the library."""
     A = synth.wide_fp32_large(1, device=DEV)
     stored, _ = _host(A)
-    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout="csc", flags=pkg.SPMV_PLAN_BANK_ORDER)
+    plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout="csc", flags=BENCH_FLAGS)
     g = torch.Generator(device=DEV)
     g.manual_seed(12)
     xh = (torch.rand(A.n, generator=g, device=DEV) * 2 - 1).cpu().pin_memory()
