@@ -484,11 +484,64 @@ def serving_measurement(pkg, dev, seconds: float = 2.0, rates=(0.5, 0.8, 1.0)):
                                  "p99_ms": round(float(np.percentile(lat, 99)), 3),
                                  "launches": st1["launches"] - st0["launches"],
                                  "max_inflight_launches": st1["max_inflight_launches"]})
+        res["check"] = serving_check(pkg, srv, ids, mats, bufs)
+        res["tracked_requests_after"] = pkg.serve_stats(srv)["tracked_requests"]
         return res
     finally:
         pkg.serve_destroy(srv)
         for p in plans:
             p.close()
+
+
+def serving_check(pkg, srv, ids, mats, bufs):
+    """Served results against the FP64 oracle at the serving workload's scale, outside the timed
+    windows: one SpMV request (2 vectors) and one SpVTM request (3 vectors) on every matrix, all
+    submitted at once so that they run mixed, each element within 1e-5 of its scale sum_j |a_ij x_j|."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from types import SimpleNamespace
+
+    cores, _ = host_cpu()
+    checks = []
+    for i in range(len(mats)):
+        for op, k in ((pkg.SPMV_OP_AX, 2), (pkg.SPMV_OP_VTA, 3)):
+            X, Y = bufs[i][op]
+            Y[64:64 + k].fill_(float("nan"))
+            checks.append((i, op, k, X[:k], Y[64:64 + k]))  # rows 64.. of the outputs are not in the ring
+    torch.cuda.synchronize()
+    rids = [pkg.serve_submit(srv, ids[i], op, k, X, Y) for i, op, k, X, Y in checks]
+    for rid in rids:
+        pkg.serve_wait(srv, rid, 600_000)
+    worst, bad, vectors = 0.0, 0, 0
+    t0 = time.time()
+    for i, A in enumerate(mats):
+        vals = A.vals.double().cpu().numpy()
+        S = synth.SparseMatrix(A.layout, A.m, A.n, A.ptr.cpu().numpy(), A.idx.cpu().numpy(), vals)
+        Sabs = SimpleNamespace(layout=A.layout, m=A.m, n=A.n, ptr=S.ptr, idx=S.idx, vals=np.abs(vals))
+        for j, op, k, X, Y in checks:
+            if j != i:
+                continue
+            for b in range(k):
+                xs = X[b].double().cpu().numpy()
+                got = Y[b].double().cpu().numpy()
+                if op == pkg.SPMV_OP_AX:
+                    ref, scale = oracle.spmv_mt(S, xs, cores), oracle.spmv_mt(Sabs, np.abs(xs), cores)
+                else:
+                    ref, scale = oracle.spvtm_mt(S, xs, cores), oracle.spvtm_mt(Sabs, np.abs(xs), cores)
+                ratio = np.abs(got - ref) / (1e-5 * scale + 1e-300)
+                ratio[np.isnan(got)] = np.inf
+                worst = max(worst, float(ratio.max()) if ratio.size else 0.0)
+                bad += int((ratio > 1.0).sum())
+                vectors += 1
+        del S, Sabs, vals
+    off_chip = sum(1 for A in mats if (A.m if A.layout == "csc" else A.n) > 24_000)
+    return {"checked_requests": len(checks), "checked_vectors": vectors, "matrices": len(mats),
+            "short_side_above_24k": off_chip, "max_err_ratio": worst, "elements_outside": bad,
+            "ok": bad == 0, "tolerance": "1e-5 x sum_j |a_ij x_j| per element, FP64 oracle",
+            "oracle_s": round(time.time() - t0, 1)}
 
 
 def run_ours(args):
@@ -698,6 +751,10 @@ def run_ours(args):
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+    chk = (extras or {}).get("serving", {}).get("check")
+    if chk is not None and not chk["ok"]:
+        print(f"served results outside the tolerance: {chk}", file=sys.stderr)
+        return 1
     return 0
 
 

@@ -119,6 +119,10 @@ typedef struct {
     int32_t tile_items;    /* nonzeros per execution tile, a multiple of 8 in [8, 992]; 0 = 512, or
                               down to 64 when nnz < 32 x 512 per SM (about two tiles per warp) */
     int32_t stages;        /* staging slots per warp (tiles in flight + 1), 2..4; 0 = 2 */
+    int32_t chunk_tiles;   /* consecutive tiles a warp streams as one processor, 1..64 (segments that
+                              run on between them are carried in registers; overlap zones arise only
+                              between chunks); 0 = 8.  The last MAX(24 (C + 1)) tiles of every CTA
+                              are single-tile chunks, which balance the warps. */
 } spmv_plan_opts;
 
 /* Summary of a plan (spmv_plan_info). */
@@ -348,7 +352,8 @@ spmv_status serve_register(serve_t srv, spmv_plan_t plan, int32_t *mat_id);
 /* Register a matrix held in HOST memory (borrowed until serve_destroy).  It is
  * copied to the device and planned when a request needs it and the budget
  * allows; idle host-registered matrices are evicted (least recently used) to
- * admit others. */
+ * admit others.  The copy and the planning run on the runtime's admission
+ * thread, so requests on resident matrices keep running meanwhile. */
 spmv_status serve_register_host(serve_t srv, int64_t m, int64_t n, int64_t nnz, int32_t layout,
                                 const int32_t *ptr, const int32_t *idx, const void *vals,
                                 int32_t val_dtype, int32_t vec_dtype, int32_t *mat_id);
@@ -359,16 +364,25 @@ spmv_status serve_register_host(serve_t srv, int64_t m, int64_t n, int64_t nnz, 
  * in + b*len_in and out + b*len_out (device memory, vec_dtype, contiguous).
  * Returns at once with *req_id.  The request joins the next launch of the same
  * (matrix, op) with room; the buffers must stay valid until it completes.
+ * The runtime reads `in` on its own streams with no ordering against the
+ * caller's: `in` must be complete on the device when serve_submit is called
+ * (synchronize the stream that produced it first).  `out` holds the results
+ * once serve_poll or serve_wait reports the request done.
  */
 spmv_status serve_submit(serve_t srv, int32_t mat_id, int32_t op, int32_t k,
                          const void *in, void *out, uint64_t *req_id);
 
 /* Non-blocking status: *done = 1 once the results are in `out`; *latency_ms =
  * submit-to-completion time (valid when done).  A finished request that failed
- * returns its error status. */
+ * returns its error status.  The first serve_poll or serve_wait that reports a
+ * request finished retires it from the runtime's request table into a window of
+ * the 65,536 most recently reported requests, which later calls still answer;
+ * after that its id is unknown (SPMV_ERR_NOT_FOUND).  A request whose completion
+ * is never asked for stays in the table until serve_destroy. */
 spmv_status serve_poll(serve_t srv, uint64_t req_id, int32_t *done, double *latency_ms);
 
-/* Block until the request completes or timeout_ms passes (SPMV_ERR_TIMEOUT). */
+/* Block until the request completes or timeout_ms passes (SPMV_ERR_TIMEOUT); on
+ * completion the request is retired as by serve_poll. */
 spmv_status serve_wait(serve_t srv, uint64_t req_id, int32_t timeout_ms);
 
 /* Counters of a serving runtime. */
@@ -377,6 +391,7 @@ typedef struct {
     int64_t admissions, evictions, resident_matrices;
     uint64_t resident_bytes;
     int32_t max_inflight_launches;
+    int64_t tracked_requests;  /* requests in the table: queued, running, or finished and not yet reported */
 } serve_stats_t;
 
 spmv_status serve_stats(serve_t srv, serve_stats_t *out);

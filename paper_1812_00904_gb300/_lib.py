@@ -38,7 +38,7 @@ class SpmvError(RuntimeError):
 
 class spmv_plan_opts(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("tile_items", ctypes.c_int32),
-                ("stages", ctypes.c_int32)]
+                ("stages", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32)]
 
 
 class spmv_plan_info_t(ctypes.Structure):
@@ -66,7 +66,8 @@ class serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("vectors", ctypes.c_int64), ("launches", ctypes.c_int64), ("admissions", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("resident_matrices", ctypes.c_int64),
-                ("resident_bytes", ctypes.c_uint64), ("max_inflight_launches", ctypes.c_int32)]
+                ("resident_bytes", ctypes.c_uint64), ("max_inflight_launches", ctypes.c_int32),
+                ("tracked_requests", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

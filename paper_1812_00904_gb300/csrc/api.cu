@@ -54,7 +54,7 @@ cudaError_t launch_stream(const spmv_plan_s *p, int mode, int kb, const LaunchAr
 int kb_template(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : 8; }
 int kb_log2(int kbt) { return kbt <= 1 ? 0 : kbt <= 2 ? 1 : kbt <= 4 ? 2 : 3; }
 
-// Tiles per chunk of the streaming kernels' full rounds: a warp carries a segment across the
+// Tiles per chunk of the streaming kernels (default): a warp carries a segment across the
 // tiles of a chunk in registers, so overlap zones (and their FP64 fix-up) arise only at chunk
 // boundaries, while the CTA's warps still stream a compact stretch of the arrays.
 constexpr int CHUNK_TILES = 8;
@@ -242,8 +242,7 @@ static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in
         a.sp.vout[b] = out[b];
     }
     set_geometry(p, a, MODE_SEGDOT, kb_template(kb));
-    const spmv_plan_s::ProcZones &pz = p->pz[kb_log2(kb_template(kb))];
-    if (pz.W * 32 != a.block) return set_error(SPMV_ERR_CUDA, "internal: zone table made for another warp count");
+    const spmv_plan_s::ProcZones &pz = p->pz;
     a.sp.nproc = pz.nproc;
     a.stream = s;
     {
@@ -460,6 +459,8 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
         return set_error(SPMV_ERR_INVALID_ARG, "tile_items must be a multiple of 8 in [8, 992]");
     if (p->S < 2 || p->S > MAX_STAGES) return set_error(SPMV_ERR_INVALID_ARG, "stages must lie in [2, 4]");
     if (W < 1 || W > MAX_WARPS) return set_error(SPMV_ERR_INVALID_ARG, "warps_per_cta must lie in [1, 24]");
+    if (opts && (opts->chunk_tiles < 0 || opts->chunk_tiles > 64))
+        return set_error(SPMV_ERR_INVALID_ARG, "chunk_tiles must lie in [0, 64]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
     p->x_cap = (int)align_up((size_t)p->T / 4 + 16, 8);  // columns of a tile's window (fall back to global beyond)
     p->smem_max = smem_max;
@@ -568,18 +569,15 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     // ---- workspace, part 2: tiles (descriptors, masks), processor zones, records and partial sums
     const int nt = p->ntiles;
     p->ctas = (pi && pi->ctas > 0) ? std::min(pi->ctas, std::max(nt, 1)) : std::max(1, std::min(sms, nt));
-    p->chunk_tiles = CHUNK_TILES;
-    // processors (warps holding tiles) of the segmented passes, per vector-slot template in use
-    const int ntpl = p->onchip ? kb_log2(kb_template(p->batch_width)) + 1 : 1;
-    std::vector<std::vector<int32_t>> pnzb(ntpl);
-    p->max_nproc = 1;
-    for (int i = 0; i < ntpl; ++i) {
-        spmv_plan_s::ProcZones &pz = p->pz[i];
-        pz.W = std::max(1, warps_for(p, MODE_SEGDOT, 1 << i));
-        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, p->chunk_tiles, nullptr);
-        pnzb[i].resize((size_t)pz.nproc + 1);
-        stream_processors(nt, p->T, (int)nnz, p->ctas, pz.W, p->chunk_tiles, pnzb[i].data());
-        p->max_nproc = std::max(p->max_nproc, pz.nproc);
+    p->chunk_tiles = (opts && opts->chunk_tiles > 0) ? opts->chunk_tiles : CHUNK_TILES;
+    // processors (chunks of tiles) of the streaming passes and their nonzero boundaries
+    std::vector<int32_t> pnzb;
+    {
+        spmv_plan_s::ProcZones &pz = p->pz;
+        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, p->chunk_tiles, nullptr);
+        pnzb.resize((size_t)pz.nproc + 1);
+        stream_processors(nt, p->T, (int)nnz, p->ctas, p->chunk_tiles, pnzb.data());
+        p->max_nproc = std::max(1, pz.nproc);
     }
     const size_t part_bytes = (pi && pi->segdot_only) ? 16
                               : p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
@@ -588,15 +586,14 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
-    size_t o_pz[4];
-    for (int i = 0; i < ntpl; ++i) o_pz[i] = carve((size_t)std::max(p->pz[i].nproc, 1) * sizeof(ZoneDev));
+    const size_t o_pz = carve((size_t)p->max_nproc * sizeof(ZoneDev));
     const size_t o_recl = carve(rec_bytes);
     const size_t o_recr = carve(rec_bytes);
     const size_t o_part = carve(std::max(part_bytes, (size_t)16));
     // set-up only
     const size_t o_tnzb = carve((size_t)(nt + 1) * 4);
     const size_t o_taux = carve((size_t)std::max(nt, 1) * sizeof(ChunkAux));
-    const size_t o_pnzb = carve((size_t)(p->max_nproc + 1) * 4 * ntpl);
+    const size_t o_pnzb = carve((size_t)(p->max_nproc + 1) * 4);
     const size_t o_paux = carve((size_t)p->max_nproc * sizeof(ChunkAux));
     const size_t o_pdev = carve((size_t)p->max_nproc * sizeof(ChunkDev));
     const size_t ws2 = off;
@@ -618,15 +615,12 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
         CUDA_TRY(launch_tile_bounds(nt, p->T, (int)nnz, tnzb, s));
         CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, nt, tnzb, p->T, taux, s));
         CUDA_TRY(launch_masks(p->pptr, taux, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
-        // the Sec. IV-B set-up over the processors of the segmented passes gives their overlap zones
-        for (int i = 0; i < ntpl; ++i) {
-            spmv_plan_s::ProcZones &pz = p->pz[i];
-            pz.zones = reinterpret_cast<ZoneDev *>(w2 + o_pz[i]);
-            int32_t *nzb_i = dpnzb + (size_t)i * (p->max_nproc + 1);
-            CUDA_TRY(cudaMemcpyAsync(nzb_i, pnzb[i].data(), ((size_t)pz.nproc + 1) * 4, cudaMemcpyHostToDevice, s));
-            CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, pz.nproc, nzb_i, p->T, paux, s));
-            CUDA_TRY(launch_setup(paux, pz.nproc, pdev, pz.zones, p->counts + 8 + 4 * i, s));
-        }
+        // the Sec. IV-B set-up over the processors (chunks) gives their overlap zones
+        spmv_plan_s::ProcZones &pz = p->pz;
+        pz.zones = reinterpret_cast<ZoneDev *>(w2 + o_pz);
+        CUDA_TRY(cudaMemcpyAsync(dpnzb, pnzb.data(), ((size_t)pz.nproc + 1) * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, pz.nproc, dpnzb, p->T, paux, s));
+        CUDA_TRY(launch_setup(paux, pz.nproc, pdev, pz.zones, p->counts + 8, s));
     }
     CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, rec_bytes, s));
     CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, rec_bytes, s));
@@ -637,7 +631,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     CUDA_TRY(cudaStreamSynchronize(s));  // also keeps pnzb alive until its copies are done
     p->z = counts[0];
     p->vmax = counts[2];
-    for (int i = 0; i < ntpl; ++i) p->pz[i].z = nt > 0 ? counts[8 + 4 * i] : 0;
+    p->pz.z = nt > 0 ? counts[8] : 0;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);

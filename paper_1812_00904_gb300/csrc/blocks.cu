@@ -52,10 +52,10 @@ __device__ __forceinline__ int block_of(int64_t k, int nt, int G, int T) {
     return t < big ? (int)(t / (q + 1)) : (int)(r + (t - big) / q);
 }
 
-// For the candidate block counts G_c = (c + 1) * sms: the widest window (segments spanned) of any
-// block.  One thread per (candidate, block).
+// For the candidate block counts G_c = (c + 1) * sms: the widest window of any block (the segments
+// it spans, from its first one rounded down to a multiple of xa).  One thread per (candidate, block).
 __global__ void block_span_kernel(const int32_t *__restrict__ pptr, int n_major, int64_t nnz, int nt, int T, int sms,
-                                  int ncand, int32_t *__restrict__ maxspan) {
+                                  int ncand, int xa, int32_t *__restrict__ maxspan) {
     const int64_t total = (int64_t)sms * ncand * (ncand + 1) / 2;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -69,14 +69,15 @@ __global__ void block_span_kernel(const int32_t *__restrict__ pptr, int n_major,
         if (G > nt) continue;
         const int64_t a = block_begin(g, nt, G, T, nnz), b = block_begin(g + 1, nt, G, T, nnz);
         if (b <= a) continue;
-        const int jf = seg_of(pptr, 0, n_major, a), jl = seg_of(pptr, 0, n_major, b - 1);
+        const int jf = seg_of(pptr, 0, n_major, a) / xa * xa, jl = seg_of(pptr, 0, n_major, b - 1);
         atomicMax(&maxspan[c], jl - jf + 1);
     }
 }
 
-// Window (first segment, number of segments) of every block for the chosen G.
+// Window (first segment, rounded down to a multiple of xa so that it starts on a 16-byte
+// boundary of the vector; number of segments) of every block for the chosen G.
 __global__ void block_window_kernel(const int32_t *__restrict__ pptr, int n_major, int64_t nnz, int nt, int T, int G,
-                                    int2 *__restrict__ win) {
+                                    int xa, int2 *__restrict__ win) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= G) return;
     const int64_t a = block_begin(g, nt, G, T, nnz), b = block_begin(g + 1, nt, G, T, nnz);
@@ -84,7 +85,7 @@ __global__ void block_window_kernel(const int32_t *__restrict__ pptr, int n_majo
         win[g] = make_int2(0, 0);
         return;
     }
-    const int jf = seg_of(pptr, 0, n_major, a), jl = seg_of(pptr, 0, n_major, b - 1);
+    const int jf = seg_of(pptr, 0, n_major, a) / xa * xa, jl = seg_of(pptr, 0, n_major, b - 1);
     win[g] = make_int2(jf, jl - jf + 1);
 }
 
@@ -129,8 +130,9 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     if (cudaMalloc(&d_max, BLOCK_CANDIDATES * 4) != cudaSuccess) return set_error(SPMV_ERR_OOM, "row blocks");
     std::vector<int32_t> mx(BLOCK_CANDIDATES, 0);
     cudaMemsetAsync(d_max, 0, BLOCK_CANDIDATES * 4, s);
+    const int xa = 16 / p->sx;
     block_span_kernel<<<std::max(1, sms * 4), 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, T, sms, BLOCK_CANDIDATES,
-                                                           d_max);
+                                                           xa, d_max);
     cudaError_t ce = cudaMemcpyAsync(mx.data(), d_max, BLOCK_CANDIDATES * 4, cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     cudaFree(d_max);
@@ -161,7 +163,7 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     int32_t *keys = nullptr;  // bmaj then bmin, nnz each
     if (cudaMalloc(&keys, (size_t)p->nnz * 8) != cudaSuccess) return set_error(SPMV_ERR_OOM, "row blocks");
     int32_t *bmaj = keys, *bmin = keys + p->nnz;
-    block_window_kernel<<<(G + 255) / 256, 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, T, G, win);
+    block_window_kernel<<<(G + 255) / 256, 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, T, G, xa, win);
     block_keys_kernel<<<std::max(1, sms * 16), 256, 0, s>>>(p->pptr, p->idx, p->n_major, n_minor, nt, T, G, win, bmaj,
                                                             bmin);
     ce = cudaGetLastError();
@@ -194,6 +196,7 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     o.tile_items = T;
     o.stages = p->S;
     o.warps_per_cta = p->W;
+    o.chunk_tiles = p->chunk_tiles;
     spmv_plan_s *q = nullptr;
     st = plan_create(&q, (int64_t)nseg, wmax, p->nnz, SPMV_CSR_TALL, bptr, sidx, svals, p->val_t, p->vec_t, s,
                      p->flags & SPMV_PLAN_BANK_ORDER, &o, &pi);

@@ -69,8 +69,8 @@ struct StreamParams {
     void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g
     void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
     void *rec_left, *rec_right;  // SEGDOT carry records [b * nproc + proc]: (hi, lo) pairs of the accumulation type
-    int32_t nproc;           // processors (chunks of tiles) of this launch: the record stride
-    int32_t chunk_tiles;     // C, tiles per chunk of the full rounds
+    int32_t nproc;           // processors (chunks of tiles) of the plan: the record stride
+    int32_t chunk_tiles;     // C, tiles per chunk (before the single-tile tail of every CTA)
     const int2 *win;         // SEGDOT over row-sorted blocks: per CTA (first element, length) of its window of
                              // the input vector; the indices are offsets into the window (NULL: whole vector)
     int32_t *err;
@@ -119,10 +119,10 @@ cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int np
                            void *const *out, cudaStream_t s);
 cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s);
-// Processors of a streaming launch with W warps per CTA: the chunks of tiles of every CTA's
-// tile range, in order (the kernel's numbering).  Fills nzb[0..nproc] (if not NULL) with
-// their nonzero boundaries; returns nproc.
-int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int C, int32_t *nzb);
+// Processors of the streaming launches: the chunks of tiles of every CTA's tile range, in
+// order (the kernel's numbering, whatever the warp count).  Fills nzb[0..nproc] (if not
+// NULL) with their nonzero boundaries; returns nproc.
+int stream_processors(int ntiles, int T, int nnz, int ctas, int C, int32_t *nzb);
 
 // Plan kernels (plan.cu).
 cudaError_t launch_validate(const int32_t *ptr, const int32_t *idx, int n_major, int nnz, int n_minor, int32_t *err,

@@ -328,13 +328,13 @@ cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles,
     return cudaGetLastError();
 }
 
-// The processors of a streaming launch with W warps per CTA, in the kernel's order:
-// CTA g takes tiles [ta, ta + nct) by the Sec. II rule over the grid; they form FR =
-// nct / (W C) rounds of W chunks of C tiles, then the L tiles left over split among the W
-// warps by the Sec. II rule (one final chunk per warp that gets a tile).
+// The processors of the streaming launches, in the kernel's order (the same for every warp
+// count): CTA g takes tiles [ta, ta + nct) by the Sec. II rule over the grid and cuts them
+// into nb chunks of C tiles followed by nct - nb C single-tile chunks, where the single
+// tiles number at least MAX_WARPS (C + 1) (or all nct).
 // nzb[q] = first nonzero of chunk q; nzb[nproc] = nnz.
-int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int C, int32_t *nzb) {
-    if (ctas < 1 || W < 1 || C < 1) return 0;
+int stream_processors(int ntiles, int T, int nnz, int ctas, int C, int32_t *nzb) {
+    if (ctas < 1 || C < 1) return 0;
     const int tq = ntiles / ctas, tr = ntiles % ctas;
     int np = 0;
     auto put = [&](int tile) {
@@ -344,9 +344,10 @@ int stream_processors(int ntiles, int T, int nnz, int ctas, int W, int C, int32_
     for (int g = 0; g < ctas; ++g) {
         const int ta = g * tq + (g < tr ? g : tr);
         const int nct = tq + (g < tr ? 1 : 0);
-        const int FR = nct / (W * C), L = nct - FR * W * C;
-        for (int j = 0; j < FR * W; ++j) put(ta + j * C);
-        for (int w = 0; w < W && w < L; ++w) put(ta + FR * W * C + w * (L / W) + (w < L % W ? w : L % W));
+        const int tail_min = MAX_WARPS * C + MAX_WARPS;
+        const int nb = (nct - (nct < tail_min ? nct : tail_min)) / C;
+        for (int j = 0; j < nb; ++j) put(ta + j * C);
+        for (int t = ta + nb * C; t < ta + nct; ++t) put(t);
     }
     if (nzb) nzb[np] = nnz;
     return np;

@@ -43,16 +43,14 @@ struct spmv_plan_s {
     int32_t *err = nullptr;
     gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
     uint32_t *masks = nullptr;
-    // Overlap zones among the processors of the segmented passes (chunks of whole tiles,
-    // contiguous Sec. II groups), one table per vector-slot template of the passes (index
-    // log2 kbt: 1, 2, 4, 8 vectors), since the chunks depend on the pass's warp count.
+    // Overlap zones among the processors of the streaming passes: the chunks of whole tiles
+    // (contiguous Sec. II groups) every CTA's tile range is cut into.
     struct ProcZones {
-        int W = 0;      // warps per CTA of those passes
         int nproc = 0;  // processors (chunks), the stride of the carry records
         int z = 0;      // overlap zones among them
         gbk::ZoneDev *zones = nullptr;
     };
-    ProcZones pz[4];
+    ProcZones pz;
     int max_nproc = 0;
     void *rec_left = nullptr, *rec_right = nullptr;  // (hi, lo) pairs of the accumulation type
     void *part = nullptr;

@@ -1,11 +1,13 @@
 // Streaming kernel: the nonzeros are cut into equal-count tiles of T nonzeros;
 // each CTA takes a contiguous range of tiles by the Sec. II rule and cuts it into
-// chunks: rounds of W chunks of C consecutive tiles, warp w taking chunk w of every
-// round (so the CTA's warps stream neighbouring parts of the arrays at any time),
-// then the tiles left over split among the W warps by the Sec. II rule, one final
-// chunk each.  Every warp gets the same number of tiles, give or take one.  The
-// chunks are the "processors" of Sec. II: contiguous groups of nonzeros, each
-// owning its own overlap-zone records.
+// chunks: nb chunks of C consecutive tiles, then a tail of single-tile chunks
+// (at least MAX_WARPS (C + 1) tiles, when the CTA has that many).  The chunks are
+// the "processors" of Sec. II: contiguous groups of nonzeros, each owning its own
+// overlap-zone records; they do not depend on the number of warps of a pass, so a
+// vector's sums come out the same in single- and multi-vector passes.  Warp w of
+// W takes the C-tile chunks w, w + W, w + 2W, ... (the CTA's warps stream
+// neighbouring parts of the arrays at any time), then a contiguous run of tail
+// tiles that brings every warp to the same tile count, give or take one.
 // Every warp streams its own tiles through S shared-memory slots of its own:
 // when it has finished a tile it issues the bulk (TMA) copies of the tile S
 // ahead into the freed slot (one copy per array: indices, values, segment-start
@@ -80,25 +82,24 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
     unsigned char *myslots = smem + p.vec_region_bytes + BAR_BYTES + (size_t)warp * S * p.slot_bytes;
 
-    // this CTA's tiles [ta, ta + nct): the Sec. II rule over the grid; FR full rounds of W
-    // chunks of C tiles, then the L tiles left, one final chunk per warp
+    // this CTA's tiles [ta, ta + nct): the Sec. II rule over the grid; nb chunks of C tiles,
+    // then nct - nb C single-tile chunks
     const int G = gridDim.x, g = blockIdx.x;
     const int tq = p.ntiles / G, tr = p.ntiles % G;
     const int ta = g * tq + min(g, tr);
     const int nct = tq + (g < tr ? 1 : 0);
     const int C = p.chunk_tiles;
-    const int FR = nct / (W * C);
-    const int L = nct - FR * W * C;
-    const int fbase = ta + FR * W * C + warp * (L / W) + min(warp, L % W);  // this warp's final chunk
-    const int nk = FR * C + L / W + (warp < L % W ? 1 : 0);                // tiles of this warp
+    auto big_chunks = [&](int n) { return (n - min(n, MAX_WARPS * C + MAX_WARPS)) / C; };
+    const int nb = big_chunks(nct);
+    const int cnt = nb / W + (warp < nb % W ? 1 : 0);    // C-tile chunks of this warp
+    const int nk = nct / W + (warp < nct % W ? 1 : 0);   // tiles of this warp
+    // first tail tile of this warp: the tiles of the warps before it less their C-tile chunks
+    const int toff = (warp * (nct / W) + min(warp, nct % W)) - C * (warp * (nb / W) + min(warp, nb % W));
     auto tile_of = [&](int k) {  // tile of this warp's k-th tile
-        return k < FR * C ? ta + ((k / C) * W + warp) * C + k % C : fbase + (k - FR * C);
+        return k < cnt * C ? ta + (warp + (k / C) * W) * C + k % C : ta + nb * C + toff + (k - cnt * C);
     };
-    // processors (chunks) before this CTA: a CTA of n tiles has FR(n) W + min(W, L(n)) chunks
-    auto chunks_of = [&](int n) {
-        const int fr = n / (W * C);
-        return fr * W + min(W, n - fr * W * C);
-    };
+    // processors (chunks) before this CTA: a CTA of n tiles has big_chunks(n) + n - C big_chunks(n)
+    auto chunks_of = [&](int n) { return n - (C - 1) * big_chunks(n); };
     const int chunk0 = g * chunks_of(tq) + min(g, tr) * (chunks_of(tq + 1) - chunks_of(tq));
 
     // this warp's slot barriers (used by this warp only)
@@ -219,7 +220,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
             AT *acc = reinterpret_cast<AT *>(smem);
             for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
         } else {
-            // the input vector, or this CTA's window of it (row-sorted blocks)
+            // the input vector, or this CTA's window of it (row-sorted blocks; its first
+            // element is 16-byte aligned)
             XT *vs = reinterpret_cast<XT *>(smem);
             int wb = 0, wl = p.n_minor;
             if (MODE == MODE_SEGDOT && p.win) {
@@ -227,10 +229,34 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 wb = w.x;
                 wl = min(w.y, p.n_minor);
             }
-            for (int i = threadIdx.x; i < wl; i += blockDim.x) {
+            if constexpr (KB == 1) {
+                // one vector: its 16-byte aligned part by bulk copies on one barrier, the rest
+                // (under 16 bytes) by plain loads
+                const XT *src = static_cast<const XT *>(p.vin[0]) + wb;
+                constexpr int xa = 16 / (int)sizeof(XT);
+                const int wbulk = wl & ~(xa - 1);
+                uint64_t *sbar = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes + BAR_BYTES) - 1;
+                if (threadIdx.x == 0 && wbulk > 0) {
+                    mbar_init(sbar, 1);
+                    fence_mbar_init();
+                    mbar_arrive_expect_tx(sbar, static_cast<uint32_t>(wbulk) * (uint32_t)sizeof(XT));
+                    constexpr int piece = 32768 / (int)sizeof(XT);
+                    for (int o = 0; o < wbulk; o += piece)
+                        bulk_g2s(vs + o, src + o, static_cast<uint32_t>(min(piece, wbulk - o)) * (uint32_t)sizeof(XT),
+                                 sbar);
+                }
+                for (int i = wbulk + threadIdx.x; i < wl; i += blockDim.x) vs[i] = src[i];
+                __syncthreads();  // the barrier's initialisation before anyone waits on it
+                if (wbulk > 0 && !mbar_wait_bounded(sbar, 0, WAIT_LIMIT_NS)) {
+                    if (threadIdx.x == 0) atomicOr(p.err, ERR_WAIT);
+                    mbar_wait_bounded(sbar, 0, WAIT_LIMIT_NS);  // let the copy land before going on
+                }
+            } else {
+                for (int i = threadIdx.x; i < wl; i += blockDim.x) {
 #pragma unroll
-                for (int b = 0; b < KB; ++b)
-                    vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[wb + i] : zero_of<XT>();
+                    for (int b = 0; b < KB; ++b)
+                        vs[i * KB + b] = (b < kb) ? static_cast<const XT *>(p.vin[b])[wb + i] : zero_of<XT>();
+                }
             }
         }
     }
@@ -281,10 +307,10 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 // position of the tile in its chunk; the chunk's first segment started in the
                 // previous chunk (left record) and its last continues in the next (right record)
                 // by the flags of the chunk's first and last tiles
-                const bool in_round = k < FR * C;
-                const bool chunk_first = in_round ? (k % C) == 0 : k == FR * C;
-                const bool chunk_last = in_round ? (k % C) == C - 1 : k == nk - 1;
-                const int proc = chunk0 + (in_round ? (k / C) * W : FR * W) + warp;
+                const bool in_big = k < cnt * C;
+                const bool chunk_first = in_big ? (k % C) == 0 : true;
+                const bool chunk_last = in_big ? (k % C) == C - 1 : true;
+                const int proc = chunk0 + (in_big ? warp + (k / C) * W : nb + toff + (k - cnt * C));
                 if (chunk_first) {
                     cfirst = i0;
                     cleft = (d.z & 1) != 0;

@@ -151,3 +151,131 @@ def test_serving_errors_are_statuses():
         assert e.value.status == 9
     finally:
         pkg.serve_destroy(srv)
+
+
+def _serving_sized():
+    """A dozen matrices of the serving workload's ranges (m 1k-50k short side, wide and tall),
+    four with a short side above what fits on chip, nonzeros kept to a few million each."""
+    specs = [("csc", 1_000, 400_000, 2_000_000), ("csr", 900_000, 1_500, 3_000_000),
+             ("csc", 4_000, 1_000_000, 4_000_000), ("csr", 2_000_000, 8_000, 5_000_000),
+             ("csc", 12_000, 300_000, 3_000_000), ("csr", 500_000, 20_000, 2_000_000),
+             ("csc", 30_000, 600_000, 4_000_000), ("csr", 700_000, 36_000, 3_000_000),
+             ("csc", 44_000, 200_000, 2_500_000), ("csr", 400_000, 50_000, 2_000_000),
+             ("csc", 2_500, 5_000_000, 6_000_000), ("csr", 3_000_000, 3_000, 4_000_000)]
+    out = []
+    for i, (layout, m, n, z) in enumerate(specs):
+        A = synth.serving_matrix(dict(id=100 + i, layout=layout, m=m, n=n, nnz=z, seed=9000 + i), device=DEV)
+        plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout=layout)
+        stored = synth.SparseMatrix(layout, A.m, A.n, A.ptr.cpu().numpy(), A.idx.cpu().numpy(),
+                                    A.vals.double().cpu().numpy())
+        out.append((A, stored, plan))
+    return out
+
+
+def test_serving_sized_matrices_alone_and_in_the_mix():
+    mats = _serving_sized()
+    assert sum(1 for A, _, p in mats if not p.info()["short_on_chip"]) >= 3  # the off-chip paths are exercised
+    rng = np.random.default_rng(17)
+    reqs = []
+    for r in range(60):
+        i = r % len(mats) if r < 2 * len(mats) else int(rng.integers(len(mats)))
+        op = (r // len(mats)) % 2 if r < 2 * len(mats) else int(rng.integers(2))  # every matrix, both ops
+        k = int(rng.integers(1, 5))
+        A = mats[i][0]
+        len_in, len_out = (A.n, A.m) if op == pkg.SPMV_OP_AX else (A.m, A.n)
+        g = torch.Generator(device=DEV)
+        g.manual_seed(3000 + r)
+        X = torch.rand((k, len_in), generator=g, device=DEV) * 2 - 1
+        Y = torch.full((k, len_out), float("nan"), device=DEV)
+        reqs.append((i, op, k, X, Y))
+    alone = []
+    for i, op, k, X, _ in reqs:
+        plan = mats[i][2]
+        alone.append(torch.stack([plan.spmv(X[b]) if op == pkg.SPMV_OP_AX else plan.spvtm(X[b]) for b in range(k)]))
+    torch.cuda.synchronize()
+    srv = pkg.serve_create(64 * GB, k_max=16, n_streams=4)
+    try:
+        ids = [pkg.serve_register(srv, plan.handle) for _, _, plan in mats]
+        rids = [pkg.serve_submit(srv, ids[i], op, k, X, Y) for i, op, k, X, Y in reqs]
+        for rid in rids:
+            pkg.serve_wait(srv, rid, 120_000)
+        st = pkg.serve_stats(srv)
+    finally:
+        pkg.serve_destroy(srv)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for (i, op, k, X, Y), ref in zip(reqs, alone):
+        A, stored, plan = mats[i]
+        for b in range(k):
+            xs = host_of(X[b])
+            if op == pkg.SPMV_OP_AX:
+                ref_o, scale = oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs)
+            else:
+                ref_o, scale = oracle.spvtm(stored, xs), oracle.abs_spvtm(stored, xs)
+            assert_close(host_of(Y[b]), ref_o, scale, 1e-5, f"served matrix {i} op {op}")
+            assert_close(host_of(Y[b]), host_of(ref[b]), scale, 1e-5, f"matrix {i} op {op} alone vs in the mix")
+        if _segmented(A.layout, op):
+            assert torch.equal(Y, ref), f"matrix {i} op {op}: segmented result differs from the single call"
+    for _, _, p in mats:
+        p.close()
+
+
+def test_resident_requests_run_while_another_matrix_is_admitted():
+    """A host-registered matrix is copied and planned on the admission thread; requests on an
+    already resident matrix submitted right after it complete before that admission ends."""
+    big = synth.wide_fp32_large(7, device=DEV, scale=0.2)  # about 40M nonzeros, 320 MB to copy
+    hp, hi, hv = big.ptr.cpu().numpy(), big.idx.cpu().numpy(), big.vals.cpu().numpy()
+    small = synth.random_matrix(500, 20_000, "csc", density=0.01, seed=71)
+    t, stored = device_matrix(small, torch.float32)
+    plan = pkg.Plan(small.m, small.n, t["ptr"], t["idx"], t["vals"])
+    srv = pkg.serve_create(64 * GB, k_max=4, n_streams=2)
+    try:
+        rid_small = pkg.serve_register(srv, plan.handle)
+        rid_big = pkg.serve_register_host(srv, big.m, big.n, big.nnz, pkg.SPMV_CSC_WIDE, hp, hi, hv, pkg.SPMV_F32,
+                                          pkg.SPMV_F32)
+        xb = torch.rand(big.n, device=DEV)
+        yb = torch.empty(big.m, device=DEV)
+        xs = [dev_vec(synth.uniform_vector(small.n, 80 + r), torch.float32) for r in range(20)]
+        ys = [torch.empty(small.m, device=DEV) for _ in range(20)]
+        torch.cuda.synchronize()
+        r_big = pkg.serve_submit(srv, rid_big, pkg.SPMV_OP_AX, 1, xb, yb)
+        r_small = [pkg.serve_submit(srv, rid_small, pkg.SPMV_OP_AX, 1, x, y) for x, y in zip(xs, ys)]
+        for r in r_small:
+            pkg.serve_wait(srv, r, 60_000)
+        admitted_meanwhile = pkg.serve_stats(srv)["admissions"]
+        pkg.serve_wait(srv, r_big, 120_000)
+        st = pkg.serve_stats(srv)
+    finally:
+        pkg.serve_destroy(srv)
+    assert admitted_meanwhile == 0, "the resident requests waited for the admission"
+    assert st["admissions"] == 1 and st["failed"] == 0
+    for x, y in zip(xs, ys):
+        xh = host_of(x)
+        assert_close(host_of(y), oracle.spmv(stored, xh), oracle.abs_spmv(stored, xh), 1e-5, "resident request")
+    plan.close()
+
+
+def test_request_table_stays_bounded():
+    """10,000 requests, each waited for: the runtime keeps none of them in its table, and a poll
+    after the wait still reports the request (from the window of recently reported ones)."""
+    A = synth.random_matrix(64, 1_000, "csc", density=0.05, seed=72)
+    t, stored = device_matrix(A, torch.float32)
+    plan = pkg.Plan(A.m, A.n, t["ptr"], t["idx"], t["vals"])
+    x = dev_vec(synth.uniform_vector(A.n, 1), torch.float32)
+    y = torch.empty((4, A.m), device=DEV)
+    torch.cuda.synchronize()
+    srv = pkg.serve_create(GB, k_max=8, n_streams=2)
+    try:
+        mid = pkg.serve_register(srv, plan.handle)
+        peak = 0
+        for r in range(10_000):
+            rid = pkg.serve_submit(srv, mid, pkg.SPMV_OP_AX, 1, x, y[r % 4])
+            pkg.serve_wait(srv, rid, 60_000)
+            if r % 1000 == 999:
+                peak = max(peak, pkg.serve_stats(srv)["tracked_requests"])
+        done, lat = pkg.serve_poll(srv, rid)
+        st = pkg.serve_stats(srv)
+    finally:
+        pkg.serve_destroy(srv)
+    assert done and lat >= 0.0
+    assert peak == 0 and st["tracked_requests"] == 0 and st["completed"] == 10_000
+    plan.close()
