@@ -52,7 +52,6 @@ cudaError_t launch_stream(const spmv_plan_s *p, int mode, int kb, const LaunchAr
 }
 
 int kb_template(int kb) { return kb <= 1 ? 1 : kb <= 2 ? 2 : kb <= 4 ? 4 : 8; }
-int kb_log2(int kbt) { return kbt <= 1 ? 0 : kbt <= 2 ? 1 : kbt <= 4 ? 2 : 3; }
 
 // Tiles per chunk of the streaming kernels (default): a warp carries a segment across the
 // tiles of a chunk in registers, so overlap zones (and their FP64 fix-up) arise only at chunk
