@@ -676,7 +676,13 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.skip_extras:
         extras = {}
         extras["ops_alone"] = ops_alone(pkg, plan, m, n, nnz)
-        extras["batched_k8"] = batched_rate(pkg, plan, m, n, nnz, 8, max(10, args.steps // 20))
+        single = {"spmv": 1e3 / extras["ops_alone"]["spmv"]["ms_median"],
+                  "spvtm": 1e3 / extras["ops_alone"]["spvtm"]["ms_median"]}
+        for kk in (8, 32):
+            br = batched_rate(pkg, plan, m, n, nnz, kk, max(10, args.steps // (5 * kk)))
+            for op in ("spmv", "spvtm"):
+                br[op]["vs_single_vector"] = round(br[op]["vectors_per_s"] / single[op], 2)
+            extras[f"batched_k{kk}"] = br
         extras["wide_fp64_small"] = small_fp64_flushed(pkg, dev)
         # least squares by CGLS on the same matrix: one SpMV + one SpVTM + vector updates per iteration
         bl = torch.rand(m, generator=g, device=dev) * 2 - 1

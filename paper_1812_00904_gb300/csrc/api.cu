@@ -121,14 +121,14 @@ SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     return g;
 }
 // On-chip short-vector bytes of a pass (accumulator of the scatter mode, input otherwise).
-size_t vec_bytes(const spmv_plan_s *p, int mode, int kbt) {
-    if (!p->onchip) return 0;
+size_t vec_bytes(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
+    if (!smemv) return 0;
     const size_t e = mode == MODE_SCATTER ? (size_t)p->sa : (size_t)p->sx;
     return align_up((size_t)p->n_minor * kbt * e, 128);
 }
 // Warps per CTA of a pass: the plan's warps, as many as the shared memory holds.
-int warps_for(const spmv_plan_s *p, int mode, int kbt) {
-    const size_t vec = vec_bytes(p, mode, kbt);
+int warps_for(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
+    const size_t vec = vec_bytes(p, mode, kbt, smemv);
     const SlotGeom g = slot_geom(p, mode, kbt);
     const size_t room = (size_t)p->smem_max > vec + BAR_BYTES ? (size_t)p->smem_max - vec - BAR_BYTES : 0;
     const int fit = (int)std::min<size_t>(room / ((size_t)p->S * g.bytes), 64);
@@ -137,12 +137,14 @@ int warps_for(const spmv_plan_s *p, int mode, int kbt) {
     return w == WARPS_REGS + 1 ? WARPS_REGS : w;
 }
 
-// Launch geometry of one streaming pass.
-void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt) {
+int warps_for(const spmv_plan_s *p, int mode, int kbt) { return warps_for(p, mode, kbt, p->onchip); }
+
+// Launch geometry of one streaming pass (the short vector on chip when smemv).
+void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt, bool smemv) {
     const SlotGeom g = slot_geom(p, mode, kbt);
-    const int W = std::max(1, warps_for(p, mode, kbt));
-    a.smemv = p->onchip;
-    a.sp.vec_region_bytes = (int)vec_bytes(p, mode, kbt);
+    const int W = std::max(1, warps_for(p, mode, kbt, smemv));
+    a.smemv = smemv;
+    a.sp.vec_region_bytes = (int)vec_bytes(p, mode, kbt, smemv);
     a.sp.slot_bytes = g.bytes;
     a.sp.off_val = g.off_val;
     a.sp.off_mask = g.off_mask;
@@ -200,7 +202,7 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     a.sp = base_params(p);
     a.sp.kb = kb;
     for (int b = 0; b < kb; ++b) a.sp.vin[b] = in[b];
-    set_geometry(p, a, MODE_SCATTER, kb_template(kb));
+    set_geometry(p, a, MODE_SCATTER, kb_template(kb), p->onchip);
     a.sp.part = p->part;
     if (!p->onchip) CUDA_TRY(cudaMemsetAsync(p->part, 0, (size_t)p->n_minor * sizeof(double), s));
     a.stream = s;
@@ -216,19 +218,59 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     return SPMV_OK;
 }
 
+// 2..KB_MAX vectors of a segmented pass read from global memory, interleaved into the plan's
+// buffer vt (in_len entries each): every nonzero fetches its index's kb entries with one or two
+// vector loads (through L2), so the matrix streams once for all of them.
+static spmv_status run_segdot_global(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
+                                     spmv_plan_s *prof, int id_dot, int id_fix, int64_t in_len) {
+    const int kbt = kb_template(kb);
+    const int64_t len = in_len >= 0 ? in_len : p->n_minor;
+    const size_t need = (size_t)std::max<int64_t>(len, 1) * KB_MAX * p->sx;
+    if (p->vt_bytes < need) {
+        if (p->vt) cudaFree(p->vt);
+        p->vt = nullptr;
+        p->vt_bytes = 0;
+        CUDA_TRY(cudaMalloc(&p->vt, need));
+        p->vt_bytes = need;
+    }
+    CUDA_TRY(launch_interleave(p->vec_t == SPMV_F64, kbt, kb, in, len, p->vt, s));
+    LaunchArgs a;
+    a.sp = base_params(p);
+    a.sp.kb = kb;
+    a.sp.vin[0] = p->vt;
+    for (int b = 0; b < kb; ++b) a.sp.vout[b] = out[b];
+    set_geometry(p, a, MODE_SEGDOT, kbt, false);
+    const spmv_plan_s::ProcZones &pz = p->pz;
+    a.sp.nproc = pz.nproc;
+    a.stream = s;
+    {
+        ProfScope ps(prof, id_dot, s);
+        CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
+    }
+    if (pz.z > 0) {
+        ProfScope ps(prof, id_fix, s);
+        CUDA_TRY(launch_fixup(p->vec_t == SPMV_F64, pz.zones, pz.z, p->rec_left, p->rec_right, pz.nproc, kb, out, s));
+    }
+    return SPMV_OK;
+}
+
 // The segmented pass (and its zone fix-up) of plan p; the launches are timed as kernels
-// id_dot / id_fix of plan `prof`.
+// id_dot / id_fix of plan `prof`.  Up to batch_width vectors run with the short vector on chip;
+// more run (up to KB_MAX per pass) with the vectors interleaved in a plan-owned global buffer
+// (in_len entries each: the short vector, or the long vector of a row-sorted copy's windows).
 static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
-                                   spmv_plan_s *prof, int id_dot, int id_fix) {
+                                   spmv_plan_s *prof, int id_dot, int id_fix, int64_t in_len) {
     const size_t out_bytes = (size_t)p->n_major * p->sx;
     if (p->nnz == 0 || p->n_minor == 0) {
         if (out_bytes)
             for (int b = 0; b < kb; ++b) CUDA_TRY(cudaMemsetAsync(out[b], 0, out_bytes, s));
         return SPMV_OK;
     }
-    if (!p->onchip && kb > 1) {
-        for (int b = 0; b < kb; ++b) {
-            spmv_status st = run_segdot_impl(p, 1, in + b, out + b, s, prof, id_dot, id_fix);
+    if (kb > KB_MAX || (kb > 1 && (!p->onchip || kb > p->batch_width))) {
+        for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
+            const int kg = std::min(KB_MAX, kb - g0);
+            spmv_status st = kg == 1 ? run_segdot_impl(p, 1, in + g0, out + g0, s, prof, id_dot, id_fix, in_len)
+                                     : run_segdot_global(p, kg, in + g0, out + g0, s, prof, id_dot, id_fix, in_len);
             if (st != SPMV_OK) return st;
         }
         return SPMV_OK;
@@ -240,7 +282,7 @@ static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in
         a.sp.vin[b] = in[b];
         a.sp.vout[b] = out[b];
     }
-    set_geometry(p, a, MODE_SEGDOT, kb_template(kb));
+    set_geometry(p, a, MODE_SEGDOT, kb_template(kb), p->onchip);
     const spmv_plan_s::ProcZones &pz = p->pz;
     a.sp.nproc = pz.nproc;
     a.stream = s;
@@ -256,22 +298,44 @@ static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in
 }
 
 spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
-    return run_segdot_impl(p, kb, in, out, s, p, 2, 3);
+    for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
+        const int kg = std::min(KB_MAX, kb - g0);
+        spmv_status st = run_segdot_impl(p, kg, in + g0, out + g0, s, p, 2, 3, -1);
+        if (st != SPMV_OK) return st;
+    }
+    return SPMV_OK;
 }
 
 // The short-vector product over the row-sorted blocks (SPMV_PLAN_ROW_BLOCKS): the sub-plan's
 // windowed segmented pass writes every block's short vector into ypart (its fix-up completes
 // the entries split between chunks), then the blocks' vectors are added in FP64 in block
-// order (Sec. III step 2).  One vector at a time: a window of several would not fit on chip.
+// order (Sec. III step 2).  One vector runs with its windows on chip; up to KB_MAX together read
+// their windows through L2 from an interleaved copy of the long vectors, into per-block vectors
+// [vector][block][n_minor] (a plan-owned buffer made on first use).
 static spmv_status run_row_blocks(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
     spmv_plan_s *q = p->tplan;
     const bool f64 = p->vec_t == SPMV_F64;
-    for (int b = 0; b < kb; ++b) {
-        void *yp = p->ypart;
-        spmv_status st = run_segdot_impl(q, 1, in + b, &yp, s, p, 5, 6);
+    const size_t nseg = (size_t)p->blocks * p->n_minor;
+    for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
+        const int kg = std::min(KB_MAX, kb - g0);
+        void *yp[KB_MAX];
+        void *base = p->ypart;
+        if (kg > 1) {
+            const size_t need = nseg * KB_MAX * p->sx;
+            if (p->ypart_k_bytes < need) {
+                if (p->ypart_k) cudaFree(p->ypart_k);
+                p->ypart_k = nullptr;
+                p->ypart_k_bytes = 0;
+                CUDA_TRY(cudaMalloc(&p->ypart_k, need));
+                p->ypart_k_bytes = need;
+            }
+            base = p->ypart_k;
+        }
+        for (int b = 0; b < kg; ++b) yp[b] = static_cast<char *>(base) + (size_t)b * nseg * p->sx;
+        spmv_status st = run_segdot_impl(q, kg, in + g0, yp, s, p, 5, 6, p->n_major);
         if (st != SPMV_OK) return st;
         ProfScope ps(p, 1, s);
-        CUDA_TRY(launch_combine(f64, f64, p->ypart, p->blocks, p->n_minor, 1, out + b, s));
+        CUDA_TRY(launch_combine(f64, f64, base, p->blocks, p->n_minor, kg, out + g0, s, (size_t)p->n_minor, nseg));
     }
     return SPMV_OK;
 }
@@ -286,7 +350,7 @@ static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, voi
     a.sp.vin[0] = csc ? r : x;
     a.sp.vin[1] = csc ? x : r;
     a.sp.vout[0] = g;
-    set_geometry(p, a, MODE_DVALUES, 1);
+    set_geometry(p, a, MODE_DVALUES, 1, p->onchip);
     a.stream = s;
     ProfScope ps(p, 4, s);
     CUDA_TRY(launch_stream(p, MODE_DVALUES, 1, a));
@@ -296,9 +360,10 @@ static spmv_status run_dvalues(spmv_plan_s *p, const void *r, const void *x, voi
 spmv_status run_op(spmv_plan_s *p, int op, int k, const void *const *in, void *const *out, cudaStream_t s) {
     const bool scatter = (op == SPMV_OP_AX) == (p->layout == SPMV_CSC_WIDE);
     if (scatter && p->tplan && p->nnz > 0) return run_row_blocks(p, k, in, out, s);
+    if (!scatter) return run_segdot(p, k, in, out, s);
     for (int g0 = 0; g0 < k; g0 += p->batch_width) {
         const int kb = std::min(p->batch_width, k - g0);
-        spmv_status st = scatter ? run_scatter(p, kb, in + g0, out + g0, s) : run_segdot(p, kb, in + g0, out + g0, s);
+        spmv_status st = run_scatter(p, kb, in + g0, out + g0, s);
         if (st != SPMV_OK) return st;
     }
     return SPMV_OK;
@@ -311,6 +376,8 @@ namespace gbk {
 void plan_free(spmv_plan_s *p) {
     if (!p) return;
     plan_free(p->tplan);
+    if (p->vt) cudaFree(p->vt);
+    if (p->ypart_k) cudaFree(p->ypart_k);
     if (p->bws) cudaFree(p->bws);
     if (p->bown) cudaFree(p->bown);
     for (auto &pr : p->prof) {
@@ -506,6 +573,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     const size_t o_chunks = carve((size_t)p->P * sizeof(ChunkDev));
     const size_t o_zones = carve((size_t)p->P * sizeof(ZoneDev));
     const size_t o_counts = carve(128);
+    const size_t o_sscr = carve(setup_scratch_bytes(p->P));
     const size_t o_err = carve(16);
     const size_t ws1 = off;
     CUDA_TRY(cudaMalloc(&p->ws, ws1));
@@ -562,7 +630,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     CUDA_TRY(cudaEventRecord(e0, s));
     CUDA_TRY(launch_pad_ptr(ptr, p->pptr, p->n_major, (int)nnz, p->pptr_len, s));
     CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, p->P, nullptr, p->T, p->aux, s));
-    CUDA_TRY(launch_setup(p->aux, p->P, p->chunks, p->zones, p->counts, s));
+    CUDA_TRY(launch_setup(p->aux, p->P, p->chunks, p->zones, p->counts, static_cast<char *>(p->ws) + o_sscr, s));
     p->ntiles = (int)nt64;
 
     // ---- workspace, part 2: tiles (descriptors, masks), processor zones, records and partial sums
@@ -581,7 +649,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     const size_t part_bytes = (pi && pi->segdot_only) ? 16
                               : p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
                                           : (size_t)p->n_minor * sizeof(double);
-    const size_t rec_bytes = (size_t)p->batch_width * p->max_nproc * 2 * p->sa;
+    const size_t rec_bytes = (size_t)KB_MAX * p->max_nproc * 2 * p->sa;  // any segmented pass: up to KB_MAX vectors
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
@@ -595,6 +663,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     const size_t o_pnzb = carve((size_t)(p->max_nproc + 1) * 4);
     const size_t o_paux = carve((size_t)p->max_nproc * sizeof(ChunkAux));
     const size_t o_pdev = carve((size_t)p->max_nproc * sizeof(ChunkDev));
+    const size_t o_pscr = carve(setup_scratch_bytes(p->max_nproc));
     const size_t ws2 = off;
     CUDA_TRY(cudaMalloc(&p->ws2, ws2));
     p->ws_bytes = ws1 + ws2;
@@ -619,7 +688,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
         pz.zones = reinterpret_cast<ZoneDev *>(w2 + o_pz);
         CUDA_TRY(cudaMemcpyAsync(dpnzb, pnzb.data(), ((size_t)pz.nproc + 1) * 4, cudaMemcpyHostToDevice, s));
         CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, pz.nproc, dpnzb, p->T, paux, s));
-        CUDA_TRY(launch_setup(paux, pz.nproc, pdev, pz.zones, p->counts + 8, s));
+        CUDA_TRY(launch_setup(paux, pz.nproc, pdev, pz.zones, p->counts + 8, w2 + o_pscr, s));
     }
     CUDA_TRY(cudaMemsetAsync(p->rec_left, 0, rec_bytes, s));
     CUDA_TRY(cudaMemsetAsync(p->rec_right, 0, rec_bytes, s));

@@ -115,39 +115,52 @@ constexpr int BLOCK_CANDIDATES = 16;
 constexpr int BLOCK_MIN_DENSITY = 8;
 
 spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
-    if (p->nnz == 0 || p->ntiles < sms) return SPMV_OK;
-    const int nt = p->ntiles, T = p->T;
+    if (p->nnz == 0) return SPMV_OK;
     const int n_minor = p->n_minor;
-    // the window budget: what the segmented pass leaves beside 16 warps of staging slots
-    const size_t slot = (size_t)p->S * (((size_t)T * 4 + 127) / 128 * 128 + ((size_t)T * p->sv + 127) / 128 * 128 +
-                                        (size_t)p->mwp * 4 + 160);
-    const size_t budget = (size_t)p->smem_max > BAR_BYTES + 16 * slot ? (size_t)p->smem_max - BAR_BYTES - 16 * slot : 0;
-    const int64_t max_elems = (int64_t)(budget / p->sx);
-    if (max_elems < 64) return SPMV_OK;
-
-    // ---- the smallest block count whose widest window fits
-    int32_t *d_max = nullptr;
-    if (cudaMalloc(&d_max, BLOCK_CANDIDATES * 4) != cudaSuccess) return set_error(SPMV_ERR_OOM, "row blocks");
-    std::vector<int32_t> mx(BLOCK_CANDIDATES, 0);
-    cudaMemsetAsync(d_max, 0, BLOCK_CANDIDATES * 4, s);
     const int xa = 16 / p->sx;
-    block_span_kernel<<<std::max(1, sms * 4), 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, T, sms, BLOCK_CANDIDATES,
-                                                           xa, d_max);
-    cudaError_t ce = cudaMemcpyAsync(mx.data(), d_max, BLOCK_CANDIDATES * 4, cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    cudaFree(d_max);
-    if (ce != cudaSuccess) return set_error(SPMV_ERR_CUDA, std::string("row blocks: ") + cudaGetErrorString(ce));
-    int G = 0, wmax = 0;
-    for (int c = 0; c < BLOCK_CANDIDATES; ++c) {
-        const int Gc = (c + 1) * sms;
-        if (Gc > nt) break;
-        if (mx[c] > 0 && mx[c] <= max_elems) {
-            G = Gc;
-            wmax = mx[c];
-            break;
+    // Candidate tilings of the copy: the plan's tile and half of it (smaller staging slots leave
+    // room for wider windows).  The widest window of every candidate block count comes from one
+    // pass over the block boundaries; one block per SM (a single wave of CTAs, and the fewest
+    // per-block vectors to add) is preferred, then the larger tile.
+    int G = 0, wmax = 0, T = 0;
+    for (int pass = 0; pass < 2 && G != sms; ++pass) {
+        const int Tc = pass == 0 ? p->T : p->T / 2;
+        if (Tc < 64 || (Tc % 8) != 0) break;
+        const int nt = (int)((p->nnz + Tc - 1) / Tc);
+        if (nt < sms) continue;
+        const int mwp = (int)(((size_t)Tc + 8 + 31) / 32 + 3) / 4 * 4;
+        // the window budget: what the segmented pass leaves beside 16 warps of staging slots
+        const size_t slot = (size_t)p->S * (((size_t)Tc * 4 + 127) / 128 * 128 +
+                                            ((size_t)Tc * p->sv + 127) / 128 * 128 + (size_t)mwp * 4 + 160);
+        const size_t budget =
+            (size_t)p->smem_max > BAR_BYTES + 16 * slot ? (size_t)p->smem_max - BAR_BYTES - 16 * slot : 0;
+        const int64_t max_elems = (int64_t)(budget / p->sx);
+        if (max_elems < 64) continue;
+        int32_t *d_max = nullptr;
+        if (cudaMalloc(&d_max, BLOCK_CANDIDATES * 4) != cudaSuccess) return set_error(SPMV_ERR_OOM, "row blocks");
+        std::vector<int32_t> mx(BLOCK_CANDIDATES, 0);
+        cudaMemsetAsync(d_max, 0, BLOCK_CANDIDATES * 4, s);
+        block_span_kernel<<<std::max(1, sms * 4), 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, Tc, sms,
+                                                               BLOCK_CANDIDATES, xa, d_max);
+        cudaError_t ce = cudaMemcpyAsync(mx.data(), d_max, BLOCK_CANDIDATES * 4, cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        cudaFree(d_max);
+        if (ce != cudaSuccess) return set_error(SPMV_ERR_CUDA, std::string("row blocks: ") + cudaGetErrorString(ce));
+        for (int c = 0; c < BLOCK_CANDIDATES; ++c) {
+            const int Gc = (c + 1) * sms;
+            if (Gc > nt) break;
+            if (mx[c] > 0 && mx[c] <= max_elems) {
+                if (G == 0 || Gc < G) {
+                    G = Gc;
+                    wmax = mx[c];
+                    T = Tc;
+                }
+                break;
+            }
         }
     }
     if (G == 0) return SPMV_OK;  // no block count gives windows that fit: keep the atomic pass
+    const int nt = (int)((p->nnz + T - 1) / T);
     if ((int64_t)G * n_minor >= (1ll << 31) - 64 || p->nnz < (int64_t)BLOCK_MIN_DENSITY * G * n_minor) return SPMV_OK;
 
     // ---- windows, per-nonzero segment and window column, stable sort into the copy
@@ -166,7 +179,7 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     block_window_kernel<<<(G + 255) / 256, 256, 0, s>>>(p->pptr, p->n_major, p->nnz, nt, T, G, xa, win);
     block_keys_kernel<<<std::max(1, sms * 16), 256, 0, s>>>(p->pptr, p->idx, p->n_major, n_minor, nt, T, G, win, bmaj,
                                                             bmin);
-    ce = cudaGetLastError();
+    cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         cudaFree(keys);
         return set_error(SPMV_ERR_CUDA, std::string("row blocks: ") + cudaGetErrorString(ce));

@@ -10,9 +10,12 @@ cudaError_t launch_stream_bf16(int mode, int kb, const LaunchArgs &a) {
         return a.smemv ? launch_one<VT, XT, MODE_DVALUES, 1, true>(a) : launch_one<VT, XT, MODE_DVALUES, 1, false>(a);
     }
     if (!a.smemv) {
-        if (kb != 1) return cudaErrorInvalidValue;
-        return mode == MODE_SCATTER ? launch_one<VT, XT, MODE_SCATTER, 1, false>(a)
-                                    : launch_one<VT, XT, MODE_SEGDOT, 1, false>(a);
+        if (mode == MODE_SCATTER) return kb == 1 ? launch_one<VT, XT, MODE_SCATTER, 1, false>(a) : cudaErrorInvalidValue;
+        // several vectors: interleaved in global memory (vin[0])
+        if (kb <= 1) return launch_one<VT, XT, MODE_SEGDOT, 1, false>(a);
+        if (kb <= 2) return launch_one<VT, XT, MODE_SEGDOT, 2, false>(a);
+        if (kb <= 4) return launch_one<VT, XT, MODE_SEGDOT, 4, false>(a);
+        return launch_one<VT, XT, MODE_SEGDOT, 8, false>(a);
     }
     if (mode == MODE_SCATTER) {
         if (kb <= 1) return launch_one<VT, XT, MODE_SCATTER, 1, true>(a);

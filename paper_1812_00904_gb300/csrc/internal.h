@@ -24,13 +24,12 @@ constexpr int WARPS_REGS = 16;   // warps per CTA up to which a kernel may use 1
 constexpr int MAX_STAGES = 4;    // slots per warp
 constexpr int BAR_BYTES = 1024;  // slot barriers at the start of the staging area
 
-// Per-chunk descriptor produced by the set-up (32 bytes).
+// Per-chunk descriptor produced by the set-up (24 bytes).
 struct ChunkDev {
     int32_t nz_begin, nz_end;   // nonzeros [nz_begin, nz_end) (Sec. II rule)
     int32_t e_begin, e_end;     // segments whose end event the chunk owns: [e_begin, e_end)
     int32_t jf;                 // first segment j^f (-1 if empty)
     int32_t flags;              // bit0 needLeft, bit1 needRight
-    int32_t tile_begin, tile_end;  // execution tiles the chunk is cut into
 };
 
 // Per-chunk quantities of the set-up (Sec. IV-B), device side.
@@ -115,8 +114,14 @@ cudaError_t launch_stream_bf16(int mode, int kb, const LaunchArgs &a);
 cudaError_t launch_stream_f16(int mode, int kb, const LaunchArgs &a);
 
 // Small kernels (small_kernels.cu).
+// out_b[i] = sum over parts q of part[q * qstride + b * bstride + i], in FP64, in part order
+// (qstride = 0: the layout [part][vector][element]).
 cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int nparts, int n_minor, int kb,
-                           void *const *out, cudaStream_t s);
+                           void *const *out, cudaStream_t s, size_t qstride = 0, size_t bstride = 0);
+// out[i * kbt + b] = in[b][i] (zeros for kb <= b < kbt), i < len: vectors interleaved for the
+// multi-vector segmented pass over global memory (kbt = 2, 4 or 8).
+cudaError_t launch_interleave(bool f64, int kbt, int kb, const void *const *in, int64_t len, void *out,
+                              cudaStream_t s);
 cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s);
 // Processors of the streaming launches: the chunks of tiles of every CTA's tile range, in
@@ -132,7 +137,11 @@ cudaError_t launch_pad_ptr(const int32_t *ptr, int32_t *pptr, int n_major, int n
 // segments, owned end events, and the number of execution tiles of at most tmax nonzeros.
 cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, const int32_t *nzb, int tmax, ChunkAux *aux,
                           cudaStream_t s);
-cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s);
+// The Sec. IV-B set-up over P chunks (multi-block scans): flags, groups, extents, descriptors,
+// zones; counts[0] = z, counts[2] = V (must be zero on entry).  scratch: setup_scratch_bytes(P).
+cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, void *scratch,
+                         cudaStream_t s);
+size_t setup_scratch_bytes(int P);
 // Execution tile boundaries tile_nzb[t] = min(t * T, nnz), t = 0..ntiles.
 cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cudaStream_t s);
 // Per tile: segment-start masks and the kernel's tile descriptors (needLeft / needRight of

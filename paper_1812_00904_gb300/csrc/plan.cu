@@ -102,9 +102,12 @@ cudaError_t launch_chunks(const int32_t *pptr, int n_major, int nnz, int P, cons
 }
 
 // ---------------------------------------------------------------------------
-// Sec. IV-B on one CTA.  Thread t owns the chunk range [t*per, (t+1)*per); each
-// scan is: local pass, sequential scan of the per-thread aggregates by thread
-// 0, local re-scan from the thread's prefix.
+// Sec. IV-B over P chunks on the whole GPU.  Chunk c's flags depend only on its
+// neighbours; the three scans (the additive scan of leftGroupEnd, the forward
+// segmented scan of (needLeft, leftGroup) and the backward one of (needRight,
+// rightGroup)) each run in three steps: every block of SU_ITEMS chunks scans its
+// own chunks and leaves an aggregate, one block scans the aggregates, and every
+// block rescans its chunks from its prefix.
 
 struct SegPair {  // (s, k) of the segmented operator o; `has` = false is the empty prefix
     int s, k, has;
@@ -121,114 +124,205 @@ __device__ __forceinline__ SegPair seg_op(SegPair a, SegPair b) {
     return r;
 }
 
-constexpr int SETUP_THREADS = 1024;
+constexpr int SU_THREADS = 256, SU_IPT = 8, SU_ITEMS = SU_THREADS * SU_IPT;
 
-__global__ void __launch_bounds__(SETUP_THREADS) setup_kernel(ChunkAux *__restrict__ aux, int P,
-                                                              ChunkDev *__restrict__ chunks,
-                                                              ZoneDev *__restrict__ zones, int32_t *counts) {
-    __shared__ int sh_a[SETUP_THREADS];
-    __shared__ int sh_b[SETUP_THREADS];
-    __shared__ SegPair sh_p[SETUP_THREADS];
-    const int t = threadIdx.x;
-    const int per = (P + SETUP_THREADS - 1) / SETUP_THREADS;
-    const int lo = min(P, t * per), hi = min(P, lo + per);
+struct AddOp {
+    __device__ __forceinline__ int operator()(int a, int b) const { return a + b; }
+};
+struct SegOp {
+    __device__ __forceinline__ SegPair operator()(SegPair a, SegPair b) const { return seg_op(a, b); }
+};
 
-    // "Determine overlap zones": needLeft / needRight from the neighbours' first and last segments
-    for (int c = lo; c < hi; ++c) {
-        ChunkAux a = aux[c];
-        const bool ne = a.nz_end > a.nz_begin;
-        a.needLeft = (c > 0 && ne && aux[c - 1].nz_end > aux[c - 1].nz_begin && a.jf == aux[c - 1].jl) ? 1 : 0;
-        a.needRight = (c < P - 1 && ne && aux[c + 1].nz_end > aux[c + 1].nz_begin && a.jl == aux[c + 1].jf) ? 1 : 0;
-        // "Determine ranks of overlap groups"
-        a.leftGroupEnd = (a.needLeft == 1 && (a.needRight == 0 || a.jf != a.jl)) ? 1 : 0;
-        aux[c].needLeft = a.needLeft;
-        aux[c].needRight = a.needRight;
-        aux[c].leftGroupEnd = a.leftGroupEnd;
-    }
-    __syncthreads();
-    // additive scans: rightGroup = inclusive scan of leftGroupEnd; tile offsets = exclusive scan of ntiles
-    int s_lge = 0, s_tiles = 0;
-    for (int c = lo; c < hi; ++c) {
-        s_lge += aux[c].leftGroupEnd;
-        s_tiles += aux[c].ntiles;
-    }
-    sh_a[t] = s_lge;
-    sh_b[t] = s_tiles;
-    __syncthreads();
-    if (t == 0) {
-        int ra = 0, rb = 0;
-        for (int i = 0; i < SETUP_THREADS; ++i) {
-            const int va = sh_a[i], vb = sh_b[i];
-            sh_a[i] = ra;
-            sh_b[i] = rb;
-            ra += va;
-            rb += vb;
+// Exclusive scan over the threads of a block (thread order), `id` the empty prefix; returns the
+// block total through *total.
+template <typename T, typename Op>
+__device__ T block_exclusive(T v, T id, Op op, T *total) {
+    __shared__ T sh[SU_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o;
+        if constexpr (sizeof(T) == sizeof(int)) {
+            o = __shfl_up_sync(0xffffffffu, inc, d);
+        } else {
+            o.s = __shfl_up_sync(0xffffffffu, inc.s, d);
+            o.k = __shfl_up_sync(0xffffffffu, inc.k, d);
+            o.has = __shfl_up_sync(0xffffffffu, inc.has, d);
         }
-        counts[0] = ra;  // z = number of overlap zones
-        counts[1] = rb;  // total tiles
+        if (lane >= d) inc = op(o, inc);
     }
+    if (lane == 31) sh[w] = inc;
     __syncthreads();
-    {
-        int ra = sh_a[t], rb = sh_b[t];
-        for (int c = lo; c < hi; ++c) {
-            ra += aux[c].leftGroupEnd;
-            aux[c].rightGroup = ra;
-            aux[c].leftGroup = ra - aux[c].leftGroupEnd;
-            chunks[c].tile_begin = rb;
-            rb += aux[c].ntiles;
-            chunks[c].tile_end = rb;
-        }
+    T wpre = id;
+    for (int q = 0; q < w; ++q) wpre = op(wpre, sh[q]);
+    T all = id;
+    for (int q = 0; q < SU_THREADS / 32; ++q) all = op(all, sh[q]);
+    T ex;
+    if constexpr (sizeof(T) == sizeof(int)) {
+        ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    } else {
+        ex.s = __shfl_up_sync(0xffffffffu, inc.s, 1);
+        ex.k = __shfl_up_sync(0xffffffffu, inc.k, 1);
+        ex.has = __shfl_up_sync(0xffffffffu, inc.has, 1);
     }
+    if (lane == 0) ex = id;
     __syncthreads();
-    // "Determine group extents": forward o-scan of (needLeft, leftGroup) -> procsOnLeft
-    {
-        SegPair agg{0, 0, 0};
-        for (int c = lo; c < hi; ++c) agg = seg_op(agg, SegPair{aux[c].needLeft, aux[c].leftGroup, 1});
-        sh_p[t] = agg;
-        __syncthreads();
-        if (t == 0) {
-            SegPair run{0, 0, 0};
-            for (int i = 0; i < SETUP_THREADS; ++i) {
-                const SegPair v = sh_p[i];
-                sh_p[i] = run;
-                run = seg_op(run, v);
-            }
-        }
-        __syncthreads();
-        SegPair run = sh_p[t];
-        for (int c = lo; c < hi; ++c) {
-            run = seg_op(run, SegPair{aux[c].needLeft, aux[c].leftGroup, 1});
-            aux[c].procsOnLeft = run.s;
-        }
-    }
-    __syncthreads();
-    // backward o-scan of (needRight, rightGroup) -> procsOnRight
-    {
-        SegPair agg{0, 0, 0};
-        for (int c = hi - 1; c >= lo; --c) agg = seg_op(agg, SegPair{aux[c].needRight, aux[c].rightGroup, 1});
-        sh_p[t] = agg;
-        __syncthreads();
-        if (t == 0) {
-            SegPair run{0, 0, 0};
-            for (int i = SETUP_THREADS - 1; i >= 0; --i) {
-                const SegPair v = sh_p[i];
-                sh_p[i] = run;
-                run = seg_op(run, v);
-            }
-        }
-        __syncthreads();
-        SegPair run = sh_p[t];
-        for (int c = hi - 1; c >= lo; --c) {
-            run = seg_op(run, SegPair{aux[c].needRight, aux[c].rightGroup, 1});
-            aux[c].procsOnRight = run.s;
-        }
-    }
-    __syncthreads();
-    // descriptors and the zone list: the chunk closing a left group names zone leftGroup
-    int vmax = 0;
-    for (int c = lo; c < hi; ++c) {
+    *total = all;
+    return op(wpre, ex);
+}
+
+// 1. "Determine overlap zones" and "determine ranks of overlap groups" (the flags), and every
+// block's sum of leftGroupEnd.
+__global__ void __launch_bounds__(SU_THREADS) setup_flags_kernel(ChunkAux *__restrict__ aux, int P,
+                                                                 int *__restrict__ blk_sum) {
+    const int c0 = blockIdx.x * SU_ITEMS + threadIdx.x * SU_IPT;
+    int sum = 0;
+    for (int i = 0; i < SU_IPT; ++i) {
+        const int c = c0 + i;
+        if (c >= P) break;
         const ChunkAux a = aux[c];
-        ChunkDev d = chunks[c];
+        const bool ne = a.nz_end > a.nz_begin;
+        const int nl = (c > 0 && ne && aux[c - 1].nz_end > aux[c - 1].nz_begin && a.jf == aux[c - 1].jl) ? 1 : 0;
+        const int nr = (c < P - 1 && ne && aux[c + 1].nz_end > aux[c + 1].nz_begin && a.jl == aux[c + 1].jf) ? 1 : 0;
+        const int lge = (nl == 1 && (nr == 0 || a.jf != a.jl)) ? 1 : 0;
+        aux[c].needLeft = nl;
+        aux[c].needRight = nr;
+        aux[c].leftGroupEnd = lge;
+        sum += lge;
+    }
+    int total;
+    block_exclusive(sum, 0, AddOp(), &total);
+    if (threadIdx.x == 0) blk_sum[blockIdx.x] = total;
+}
+
+// 2, 4. One block: exclusive scans of the block aggregates (additive; or segmented forward
+// and backward), in place.
+__global__ void __launch_bounds__(SU_THREADS) setup_scan_add_kernel(int *__restrict__ blk, int nb, int32_t *counts) {
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nb; base += SU_THREADS) {
+        const int i = base + threadIdx.x;
+        const int v = i < nb ? blk[i] : 0;
+        int total;
+        const int ex = block_exclusive(v, 0, AddOp(), &total);
+        if (i < nb) blk[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[0] = carry;  // z = number of overlap zones
+}
+
+__global__ void __launch_bounds__(SU_THREADS) setup_scan_seg_kernel(SegPair *__restrict__ fwd, SegPair *__restrict__ bwd,
+                                                                    int nb) {
+    __shared__ SegPair carry;
+    const SegPair id{0, 0, 0};
+    // forward, in block order
+    if (threadIdx.x == 0) carry = id;
+    __syncthreads();
+    for (int base = 0; base < nb; base += SU_THREADS) {
+        const int i = base + threadIdx.x;
+        const SegPair v = i < nb ? fwd[i] : id;
+        SegPair total;
+        const SegPair ex = block_exclusive(v, id, SegOp(), &total);
+        if (i < nb) fwd[i] = seg_op(carry, ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry = seg_op(carry, total);
+        __syncthreads();
+    }
+    // backward: element i of the reversed order is block nb - 1 - i
+    if (threadIdx.x == 0) carry = id;
+    __syncthreads();
+    for (int base = 0; base < nb; base += SU_THREADS) {
+        const int i = base + threadIdx.x;
+        const SegPair v = i < nb ? bwd[nb - 1 - i] : id;
+        SegPair total;
+        const SegPair ex = block_exclusive(v, id, SegOp(), &total);
+        if (i < nb) bwd[nb - 1 - i] = seg_op(carry, ex);
+        __syncthreads();
+        if (threadIdx.x == 0) carry = seg_op(carry, total);
+        __syncthreads();
+    }
+}
+
+// 3. rightGroup (inclusive scan of leftGroupEnd from the block's prefix) and leftGroup; every
+// block's aggregates of (needLeft, leftGroup) in order and of (needRight, rightGroup) in reverse order.
+__global__ void __launch_bounds__(SU_THREADS) setup_groups_kernel(ChunkAux *__restrict__ aux, int P,
+                                                                  const int *__restrict__ blk_pre,
+                                                                  SegPair *__restrict__ fwd, SegPair *__restrict__ bwd) {
+    const int c0 = blockIdx.x * SU_ITEMS + threadIdx.x * SU_IPT;
+    int sum = 0;
+    for (int i = 0; i < SU_IPT && c0 + i < P; ++i) sum += aux[c0 + i].leftGroupEnd;
+    int total;
+    int run = blk_pre[blockIdx.x] + block_exclusive(sum, 0, AddOp(), &total);
+    const SegPair id{0, 0, 0};
+    SegPair f = id;
+    for (int i = 0; i < SU_IPT && c0 + i < P; ++i) {
+        const int c = c0 + i;
+        const int lge = aux[c].leftGroupEnd;
+        run += lge;
+        aux[c].rightGroup = run;
+        aux[c].leftGroup = run - lge;
+        f = seg_op(f, SegPair{aux[c].needLeft, run - lge, 1});
+    }
+    SegPair ft;
+    block_exclusive(f, id, SegOp(), &ft);
+    // backward aggregate: this block's chunks from the last to the first, thread t taking the
+    // chunks thread SU_THREADS - 1 - t wrote above
+    __syncthreads();
+    SegPair b = id;
+    const int c1 = blockIdx.x * SU_ITEMS + (SU_THREADS - 1 - threadIdx.x) * SU_IPT;
+    for (int i = SU_IPT - 1; i >= 0; --i) {
+        const int c = c1 + i;
+        if (c < P) b = seg_op(b, SegPair{aux[c].needRight, aux[c].rightGroup, 1});
+    }
+    SegPair bt;
+    block_exclusive(b, id, SegOp(), &bt);
+    if (threadIdx.x == 0) {
+        fwd[blockIdx.x] = ft;
+        bwd[blockIdx.x] = bt;
+    }
+}
+
+// 5. procsOnLeft / procsOnRight from the blocks' prefixes, the descriptors, the zone list
+// (the chunk closing a left group names zone leftGroup) and V = max |S_k|.
+__global__ void __launch_bounds__(SU_THREADS) setup_extents_kernel(ChunkAux *__restrict__ aux, int P,
+                                                                   const SegPair *__restrict__ fwd,
+                                                                   const SegPair *__restrict__ bwd,
+                                                                   ChunkDev *__restrict__ chunks,
+                                                                   ZoneDev *__restrict__ zones, int32_t *counts) {
+    const SegPair id{0, 0, 0};
+    const int c0 = blockIdx.x * SU_ITEMS + threadIdx.x * SU_IPT;
+    // forward: procsOnLeft
+    SegPair f = id;
+    for (int i = 0; i < SU_IPT && c0 + i < P; ++i) f = seg_op(f, SegPair{aux[c0 + i].needLeft, aux[c0 + i].leftGroup, 1});
+    SegPair tot;
+    SegPair run = seg_op(fwd[blockIdx.x], block_exclusive(f, id, SegOp(), &tot));
+    for (int i = 0; i < SU_IPT && c0 + i < P; ++i) {
+        const int c = c0 + i;
+        run = seg_op(run, SegPair{aux[c].needLeft, aux[c].leftGroup, 1});
+        aux[c].procsOnLeft = run.s;
+    }
+    // backward: procsOnRight (threads and chunks in reverse order)
+    const int c1 = blockIdx.x * SU_ITEMS + (SU_THREADS - 1 - threadIdx.x) * SU_IPT;
+    SegPair b = id;
+    for (int i = SU_IPT - 1; i >= 0; --i)
+        if (c1 + i < P) b = seg_op(b, SegPair{aux[c1 + i].needRight, aux[c1 + i].rightGroup, 1});
+    run = seg_op(bwd[blockIdx.x], block_exclusive(b, id, SegOp(), &tot));
+    for (int i = SU_IPT - 1; i >= 0; --i) {
+        const int c = c1 + i;
+        if (c >= P) continue;
+        run = seg_op(run, SegPair{aux[c].needRight, aux[c].rightGroup, 1});
+        aux[c].procsOnRight = run.s;
+    }
+    __syncthreads();
+    int vmax = 0;
+    for (int i = 0; i < SU_IPT && c0 + i < P; ++i) {
+        const int c = c0 + i;
+        const ChunkAux a = aux[c];
+        ChunkDev d;
         d.nz_begin = a.nz_begin;
         d.nz_end = a.nz_end;
         d.e_begin = a.e_begin;
@@ -246,18 +340,27 @@ __global__ void __launch_bounds__(SETUP_THREADS) setup_kernel(ChunkAux *__restri
             vmax = max(vmax, a.procsOnLeft + 1);
         }
     }
-    sh_a[t] = vmax;
-    __syncthreads();
-    if (t == 0) {
-        int v = 0;
-        for (int i = 0; i < SETUP_THREADS; ++i) v = max(v, sh_a[i]);
-        counts[2] = v;  // V = max |S_k|
-    }
+    if (vmax) atomicMax(&counts[2], vmax);  // V = max |S_k|
 }
 
-cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, cudaStream_t s) {
-    setup_kernel<<<1, SETUP_THREADS, 0, s>>>(aux, P, chunks, zones, counts);
+cudaError_t launch_setup(ChunkAux *aux, int P, ChunkDev *chunks, ZoneDev *zones, int32_t *counts, void *scratch,
+                         cudaStream_t s) {
+    if (P <= 0) return cudaSuccess;
+    const int nb = (P + SU_ITEMS - 1) / SU_ITEMS;
+    int *blk = static_cast<int *>(scratch);
+    SegPair *fwd = reinterpret_cast<SegPair *>(blk + ((nb + 3) & ~3));
+    SegPair *bwd = fwd + nb;
+    setup_flags_kernel<<<nb, SU_THREADS, 0, s>>>(aux, P, blk);
+    setup_scan_add_kernel<<<1, SU_THREADS, 0, s>>>(blk, nb, counts);
+    setup_groups_kernel<<<nb, SU_THREADS, 0, s>>>(aux, P, blk, fwd, bwd);
+    setup_scan_seg_kernel<<<1, SU_THREADS, 0, s>>>(fwd, bwd, nb);
+    setup_extents_kernel<<<nb, SU_THREADS, 0, s>>>(aux, P, fwd, bwd, chunks, zones, counts);
     return cudaGetLastError();
+}
+
+size_t setup_scratch_bytes(int P) {
+    const int nb = (P + SU_ITEMS - 1) / SU_ITEMS;
+    return (size_t)((nb + 3) & ~3) * sizeof(int) + 2 * (size_t)nb * sizeof(SegPair) + 64;
 }
 
 // Execution tile boundaries: tile t covers nonzeros [t*T, min((t+1)*T, nnz)), so

@@ -6,6 +6,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace gbk {
@@ -13,25 +15,27 @@ namespace gbk {
 struct OutPtrs {
     void *p[KB_MAX];
 };
+struct InPtrs {
+    const void *p[KB_MAX];
+};
 
-// out_b[i] = sum_{q < nparts} part[(q * kb + b) * n_minor + i].  A block takes 32
+// out_b[i] = sum_{q < nparts} part[q * qstride + b * bstride + i].  A block takes 32
 // consecutive elements; its 8 thread rows sum the partials q = row, row + 8, ... in
 // FP64 and the 8 row sums are added in row order: a fixed order, independent of
 // timing.  Partials of any type are widened to FP64 before they are added.
 constexpr int COMB_X = 32, COMB_Y = 8;
 template <typename XT, typename PT>
 __global__ void __launch_bounds__(COMB_X * COMB_Y) combine_kernel(const PT *__restrict__ part, int nparts, int n_minor,
-                                                                  int kb, OutPtrs out) {
+                                                                  size_t qstride, size_t bstride, OutPtrs out) {
     __shared__ double sh_s[COMB_Y][COMB_X];
     const int i = blockIdx.x * COMB_X + threadIdx.x;
     const int b = blockIdx.y;
     const int row = threadIdx.y;
     double s = 0.0;
     if (i < n_minor) {
-        const PT *src = part + (size_t)b * n_minor + i;
-        const size_t stride = (size_t)kb * n_minor;
+        const PT *src = part + (size_t)b * bstride + i;
 #pragma unroll 4
-        for (int q = row; q < nparts; q += COMB_Y) s += static_cast<double>(__ldg(src + (size_t)q * stride));
+        for (int q = row; q < nparts; q += COMB_Y) s += static_cast<double>(__ldg(src + (size_t)q * qstride));
     }
     sh_s[row][threadIdx.x] = s;
     __syncthreads();
@@ -84,17 +88,58 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
 }
 
 cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int nparts, int n_minor, int kb,
-                           void *const *out, cudaStream_t s) {
+                           void *const *out, cudaStream_t s, size_t qstride, size_t bstride) {
     if (n_minor <= 0) return cudaSuccess;
     OutPtrs o;
     for (int b = 0; b < KB_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
+    if (qstride == 0) {  // [part][vector][element]
+        qstride = (size_t)kb * n_minor;
+        bstride = (size_t)n_minor;
+    }
     const dim3 grid((n_minor + COMB_X - 1) / COMB_X, kb), block(COMB_X, COMB_Y);
     if (vec_f64) {
-        combine_kernel<double, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
+        combine_kernel<double, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor,
+                                                               qstride, bstride, o);
     } else if (part_f64) {
-        combine_kernel<float, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor, kb, o);
+        combine_kernel<float, double><<<grid, block, 0, s>>>(static_cast<const double *>(part), nparts, n_minor,
+                                                              qstride, bstride, o);
     } else {
-        combine_kernel<float, float><<<grid, block, 0, s>>>(static_cast<const float *>(part), nparts, n_minor, kb, o);
+        combine_kernel<float, float><<<grid, block, 0, s>>>(static_cast<const float *>(part), nparts, n_minor,
+                                                             qstride, bstride, o);
+    }
+    return cudaGetLastError();
+}
+
+// out[i * KB + b] = in_b[i] for b < kb, 0 for kb <= b < KB: k vectors interleaved for the
+// multi-vector segmented pass over vectors kept in global memory.
+template <typename XT, int KB>
+__global__ void interleave_kernel(InPtrs in, int kb, int64_t len, XT *__restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        XT v[KB];
+#pragma unroll
+        for (int b = 0; b < KB; ++b) v[b] = b < kb ? static_cast<const XT *>(in.p[b])[i] : XT(0);
+#pragma unroll
+        for (int b = 0; b < KB; ++b) out[i * KB + b] = v[b];
+    }
+}
+
+cudaError_t launch_interleave(bool f64, int kbt, int kb, const void *const *in, int64_t len, void *out,
+                              cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    InPtrs ip;
+    for (int b = 0; b < KB_MAX; ++b) ip.p[b] = b < kb ? in[b] : nullptr;
+    const int grid = (int)std::min<int64_t>((len + 255) / 256, 152 * 16);
+    if (f64) {
+        double *o = static_cast<double *>(out);
+        if (kbt == 2) interleave_kernel<double, 2><<<grid, 256, 0, s>>>(ip, kb, len, o);
+        else if (kbt == 4) interleave_kernel<double, 4><<<grid, 256, 0, s>>>(ip, kb, len, o);
+        else interleave_kernel<double, 8><<<grid, 256, 0, s>>>(ip, kb, len, o);
+    } else {
+        float *o = static_cast<float *>(out);
+        if (kbt == 2) interleave_kernel<float, 2><<<grid, 256, 0, s>>>(ip, kb, len, o);
+        else if (kbt == 4) interleave_kernel<float, 4><<<grid, 256, 0, s>>>(ip, kb, len, o);
+        else interleave_kernel<float, 8><<<grid, 256, 0, s>>>(ip, kb, len, o);
     }
     return cudaGetLastError();
 }

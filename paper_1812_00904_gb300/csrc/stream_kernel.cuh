@@ -59,6 +59,26 @@ template <> struct Pair<double> { using type = double2; };
 __device__ __forceinline__ float2 make_pair2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 make_pair2(double a, double b) { return make_double2(a, b); }
 
+// KB consecutive vector entries at a 16-byte aligned address (KB >= 2), by vector loads
+// through the read-only path.
+template <typename XT, int KB> struct Gather {
+    __device__ __forceinline__ static void run(const XT *src, XT (&w)[KB]) {
+        static_assert(sizeof(XT) * KB % 16 == 0 || sizeof(XT) * KB == 8, "vector loads of whole 8/16 bytes");
+        if constexpr (sizeof(XT) * KB == 8) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2 *>(src));
+            const unsigned u[2] = {q.x, q.y};
+            memcpy(w, u, 8);
+        } else {
+#pragma unroll
+            for (int h = 0; h < (int)(sizeof(XT) * KB / 16); ++h) {
+                const uint4 q = __ldg(reinterpret_cast<const uint4 *>(src) + h);
+                const unsigned u[4] = {q.x, q.y, q.z, q.w};
+                memcpy(reinterpret_cast<unsigned char *>(w) + 16 * h, u, 16);
+            }
+        }
+    }
+};
+
 template <bool B> struct BoolC {
     static constexpr bool value = B;
 };
@@ -109,31 +129,41 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     }
     __syncwarp();
 
-    // ---- tile descriptors of this warp, 32 per batch: lane j holds tile 32 * batch + j
-    int4 dcur = make_int4(0, 0, 0, 0), dnxt = make_int4(0, 0, 0, 0);  // nzb, e_begin, flags, next tile's nzb
-    int ecur = 0, enxt = 0;                                            // next tile's e_begin
-    auto load_batch = [&](int bi, int4 &d, int &e1) {
+    // ---- tile descriptors of this warp, 32 per batch: lane j holds tile 32 * batch + j: its
+    // nzb, e_begin, flags and the next tile's nzb (d); the next tile's e_begin, the tile's
+    // number and its chunk's processor number and place (e: proc << 2 | first | last << 1),
+    // worked out here once per 32 tiles
+    int4 dcur = make_int4(0, 0, 0, 0), dnxt = make_int4(0, 0, 0, 0);
+    int4 ecur = make_int4(0, 0, 0, 0), enxt = make_int4(0, 0, 0, 0);
+    auto load_batch = [&](int bi, int4 &d, int4 &e) {
         const int k = (bi << 5) + lane;
         if (k < nk) {
             const int t = tile_of(k);
             const TileMeta a = p.meta[t];
             const TileMeta b = p.meta[t + 1];
             d = make_int4(a.nzb, a.e_begin, a.flags, b.nzb);
-            e1 = b.e_begin;
+            const bool in_big = k < cnt * C;
+            const int q = k / C, o = k - q * C;
+            const int first = in_big ? (o == 0) : 1;
+            const int last = in_big ? (o == C - 1) : 1;
+            const int proc = chunk0 + (in_big ? warp + q * W : nb + toff + (k - cnt * C));
+            e = make_int4(b.e_begin, t, (proc << 2) | first | (last << 1), 0);
         }
     };
     int cb = 0;  // batch held in dcur
     load_batch(0, dcur, ecur);
     load_batch(1, dnxt, enxt);
     // descriptor of this warp's tile k (its batch is cb or cb + 1)
-    auto desc = [&](int k, int4 &d, int &e1) {
+    auto desc = [&](int k, int4 &d, int4 &e) {
         const bool c = (k >> 5) == cb;
         const int src = k & 31;
         d.x = __shfl_sync(FULL, c ? dcur.x : dnxt.x, src);
         d.y = __shfl_sync(FULL, c ? dcur.y : dnxt.y, src);
         d.z = __shfl_sync(FULL, c ? dcur.z : dnxt.z, src);
         d.w = __shfl_sync(FULL, c ? dcur.w : dnxt.w, src);
-        e1 = __shfl_sync(FULL, c ? ecur : enxt, src);
+        e.x = __shfl_sync(FULL, c ? ecur.x : enxt.x, src);
+        e.y = __shfl_sync(FULL, c ? ecur.y : enxt.y, src);
+        e.z = __shfl_sync(FULL, c ? ecur.z : enxt.z, src);
     };
     // window [xbase, xbase + nxc) of the long vector covering segments i0..i1 (16-byte aligned)
     auto xwindow = [&](int i0, int i1, int &xbase, int &nxc) {
@@ -173,16 +203,16 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     const int c_lim = c_len & ~(16 / c_es - 1);  // the array's last 16-byte boundary (in elements)
     // issue the copies of tile k into slot s
     auto issue = [&](int k, int s) {
-        int4 d;
-        int e1;
-        desc(k, d, e1);
+        int4 d, e;
+        desc(k, d, e);
+        const int e1 = e.x;
         const int kb0 = d.x & ~7;
         const int ncov = ((d.w + 7) & ~7) - kb0;
         int xbase, nxc;
         xwindow(d.y, e1, xbase, nxc);
         int e0 = kb0, cnt = ncov;
         if (lane == 2) {
-            e0 = tile_of(k) * p.mwp;
+            e0 = e.y * p.mwp;
             cnt = p.mwp;
         } else if (lane >= 3) {
             e0 = xbase;
@@ -204,7 +234,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         if (lane == 0) {  // the tile's header, read by this warp when it processes the tile
             int4 *hd = reinterpret_cast<int4 *>(myslots + (size_t)s * p.slot_bytes + p.off_hdr);
             hd[0] = d;
-            hd[1] = make_int4(e1, xbase, nxc, 0);
+            hd[1] = make_int4(e1, xbase, nxc, e.z);
         }
         __syncwarp();
         // releases the header and the plain stores; the bulk bytes complete the phase
@@ -307,10 +337,9 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 // position of the tile in its chunk; the chunk's first segment started in the
                 // previous chunk (left record) and its last continues in the next (right record)
                 // by the flags of the chunk's first and last tiles
-                const bool in_big = k < cnt * C;
-                const bool chunk_first = in_big ? (k % C) == 0 : true;
-                const bool chunk_last = in_big ? (k % C) == C - 1 : true;
-                const int proc = chunk0 + (in_big ? warp + (k / C) * W : nb + toff + (k - cnt * C));
+                const bool chunk_first = (d1.w & 1) != 0;
+                const bool chunk_last = (d1.w & 2) != 0;
+                const int proc = d1.w >> 2;
                 if (chunk_first) {
                     cfirst = i0;
                     cleft = (d.z & 1) != 0;
@@ -603,6 +632,32 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     int ix[8];
                     AT va[8];
                     const uint32_t vm_r = step_load(full_tag, check_tag, p0, rot4(vm, sw), ix, va);
+                    if constexpr (!SMEMV && KB > 1) {
+                        // several vectors in global memory, interleaved (vin[0][i * KB + b]): the
+                        // KB entries of a nonzero's index come in one or two vector loads.  The
+                        // positions run outside and the vectors inside; every vector's products
+                        // and prefix sums are the same operations as in the other paths.
+                        const XT *vt = static_cast<const XT *>(p.vin[0]);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int r = e ^ (sw << 2);  // register of position e
+                            const int ixe = sw ? ix[e ^ 4] : ix[e];
+                            const AT vae = sw ? va[e ^ 4] : va[e];
+                            XT wv[KB];
+                            if (WHOLE || ((vm_r >> r) & 1u)) {
+                                Gather<XT, KB>::run(vt + (size_t)(vwin + ixe) * KB, wv);
+                            } else {
+#pragma unroll
+                                for (int b = 0; b < KB; ++b) wv[b] = zero_of<XT>();
+                            }
+#pragma unroll
+                            for (int b = 0; b < KB; ++b) {
+                                const AT pe = vae * static_cast<AT>(wv[b]);
+                                rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pe : rr[e > 0 ? e - 1 : 0][b] + pe;
+                            }
+                        }
+                        return;
+                    }
 #pragma unroll
                     for (int b = 0; b < KB; ++b) {
                         AT pr[8];
