@@ -567,7 +567,7 @@ def run_ours(args):
     A = synth.wide_fp32_large(1, device=dev, scale=args.scale)  # every rank holds its own replica
     m, n, nnz = A.m, A.n, A.nnz
     order = 0 if args.stored_order else pkg.SPMV_PLAN_BANK_ORDER
-    blocks = 0 if args.atomic_scatter else pkg.SPMV_PLAN_ROW_BLOCKS
+    blocks = pkg.SPMV_PLAN_ROW_BLOCKS if args.row_blocks else 0
     plan = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order | blocks, warps_per_cta=args.warps,
                     tile_items=args.tile_items, stages=args.stages)
     info = plan.info()
@@ -698,11 +698,14 @@ def run_ours(args):
             ps = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=blocks)
             extras["stored_order"] = time_pair_gbs(pkg, ps, m, n, nnz, "csc", max(20, args.steps // 5))
             ps.close()
-        # SpMV by shared-memory atomic accumulation (no row-sorted copy)
-        if blocks:
-            pa = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=order)
-            extras["atomic_scatter"] = time_pair_gbs(pkg, pa, m, n, nnz, "csc", max(20, args.steps // 5))
-            pa.close()
+        # the other SpMV local step: the row-sorted copy, or shared-memory atomic accumulation
+        other = order | (0 if blocks else pkg.SPMV_PLAN_ROW_BLOCKS)
+        pa = pkg.Plan(m, n, A.ptr, A.idx, A.vals, layout="csc", flags=other)
+        pinfo = pa.info()
+        extras["atomic_scatter" if blocks else "row_blocks"] = dict(
+            time_pair_gbs(pkg, pa, m, n, nnz, "csc", max(20, args.steps // 5)),
+            blocks=pinfo["row_blocks"], widest_window=pinfo["row_block_window"])
+        pa.close()
         vb = A.vals.to(torch.bfloat16)
         pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32, flags=order | blocks)
         extras["bf16_values"] = dict(time_pair_gbs(pkg, pb, m, n, nnz, "csc", max(20, args.steps // 5), sv=2),
@@ -784,8 +787,8 @@ def main(argv=None):
     ap.add_argument("--stages", type=int, default=0, help="staging buffers per warp; 0 = library default")
     ap.add_argument("--stored-order", action="store_true",
                     help="multiply in the stored nonzero order (no bank-ordered plan copy)")
-    ap.add_argument("--atomic-scatter", action="store_true",
-                    help="SpMV by shared-memory atomic accumulation (no row-sorted plan copy)")
+    ap.add_argument("--row-blocks", action="store_true",
+                    help="SpMV over the row-sorted plan copy (SPMV_PLAN_ROW_BLOCKS) instead of shared-memory atomics")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

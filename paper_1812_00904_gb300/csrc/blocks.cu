@@ -118,13 +118,12 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     if (p->nnz == 0) return SPMV_OK;
     const int n_minor = p->n_minor;
     const int xa = 16 / p->sx;
-    // Candidate tilings of the copy: the plan's tile and half of it (smaller staging slots leave
-    // room for wider windows).  The widest window of every candidate block count comes from one
-    // pass over the block boundaries; one block per SM (a single wave of CTAs, and the fewest
-    // per-block vectors to add) is preferred, then the larger tile.
+    // The copy is tiled like the plan (half tiles, which leave room for wider windows, measured
+    // much slower per nonzero).  The widest window of every candidate block count comes from one
+    // pass over the block boundaries; the smallest count whose windows fit is taken.
     int G = 0, wmax = 0, T = 0;
-    for (int pass = 0; pass < 2 && G != sms; ++pass) {
-        const int Tc = pass == 0 ? p->T : p->T / 2;
+    for (int pass = 0; pass < 1; ++pass) {
+        const int Tc = p->T;
         if (Tc < 64 || (Tc % 8) != 0) break;
         const int nt = (int)((p->nnz + Tc - 1) / Tc);
         if (nt < sms) continue;

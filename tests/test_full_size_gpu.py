@@ -24,8 +24,8 @@ def _host(A, vals_dtype=None):
                               v.double().cpu().numpy()), v
 
 
-# the benchmark's plans: bank-ordered nonzeros and the row-sorted copy for the short-vector product
-BENCH_FLAGS = pkg.SPMV_PLAN_BANK_ORDER | pkg.SPMV_PLAN_ROW_BLOCKS
+# the benchmark's plans: bank-ordered nonzeros (its row-block variant adds the row-sorted copy)
+BENCH_FLAGS = pkg.SPMV_PLAN_BANK_ORDER
 
 
 def _check(A, val_dtype, what, flags=BENCH_FLAGS):
@@ -55,13 +55,19 @@ def test_wide_fp32_full_size():
     A = synth.wide_fp32_large(1, device=DEV)
     _, info = _check(A, None, "wide fp32")
     assert info["tile_items"] == 512 and info["stages"] == 2  # the benchmark's configuration
+
+
+def test_wide_fp32_full_size_row_blocks():
+    """The same matrix with the row-sorted copy: SpMV as segmented dot products over block windows."""
+    A = synth.wide_fp32_large(1, device=DEV)
+    _, info = _check(A, None, "wide fp32 row blocks", flags=BENCH_FLAGS | pkg.SPMV_PLAN_ROW_BLOCKS)
     assert info["row_blocks"] > 0
 
 
-def test_wide_fp32_full_size_atomic_path():
-    """The same matrix without the copies: SpMV by shared-memory atomic accumulation."""
+def test_wide_fp32_full_size_stored_order():
+    """The same matrix in the caller's order, no plan-owned copies."""
     A = synth.wide_fp32_large(1, device=DEV)
-    _, info = _check(A, None, "wide fp32 atomic", flags=0)
+    _, info = _check(A, None, "wide fp32 stored order", flags=0)
     assert info["row_blocks"] == 0
 
 
@@ -77,7 +83,8 @@ def test_wide_bf16_values_full_size():
 
 def test_tall_fp32_full_size():
     A = synth.tall_fp32_large(2, device=DEV)
-    _, info = _check(A, None, "tall fp32")
+    _check(A, None, "tall fp32")
+    _, info = _check(A, None, "tall fp32 row blocks", flags=BENCH_FLAGS | pkg.SPMV_PLAN_ROW_BLOCKS)
     assert info["row_blocks"] > 0
 
 

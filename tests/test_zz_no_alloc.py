@@ -53,3 +53,24 @@ def test_noalloc_rejects_oversized_short_dimension():
     y = torch.zeros(A.m, device=DEV)
     assert _call_noalloc(A, t, x, y) == _lib.SPMV_ERR_INVALID_ARG
     assert "49152" in _lib.load().spmv_last_error().decode()
+
+
+def test_noalloc_skips_rows_outside_the_matrix():
+    """Nothing is validated on this path: a nonzero whose row index lies outside [0, m) is
+    skipped, so the result is the product of the matrix without those entries."""
+    A = synth.random_matrix(700, 20_000, "csc", density=0.01, seed=31)
+    idx = np.asarray(A.idx, np.int32).copy()
+    bad = np.arange(0, A.nnz, 97)
+    idx[bad] = A.m + 5 + (bad % 3)  # rows past the end of y
+    vals = np.asarray(A.vals, np.float32)
+    t = {"ptr": torch.from_numpy(np.asarray(A.ptr, np.int32)).to(DEV), "idx": torch.from_numpy(idx).to(DEV),
+         "vals": torch.from_numpy(vals).to(DEV)}
+    x = dev_vec(synth.uniform_vector(A.n, 33), torch.float32)
+    y = torch.full((A.m,), float("nan"), dtype=torch.float32, device=DEV)
+    assert _call_noalloc(A, t, x, y) == 0
+    torch.cuda.synchronize()
+    kept = vals.astype(np.float64).copy()
+    kept[bad] = 0.0
+    ref_m = synth.SparseMatrix("csc", A.m, A.n, A.ptr, np.where(idx < A.m, idx, 0).astype(np.int32), kept)
+    xs = host_of(x)
+    assert_close(host_of(y), oracle.spmv(ref_m, xs), oracle.abs_spmv(ref_m, xs) + 1e-30, 1e-5, "rows outside skipped")
