@@ -123,10 +123,6 @@ typedef struct {
                               run on between them are carried in registers; overlap zones arise only
                               between chunks); 0 = 8.  The last MAX(24 (C + 1)) tiles of every CTA
                               are single-tile chunks, which balance the warps. */
-    int32_t scatter_loads; /* 1: the single-vector pass that accumulates into the short vector in shared
-                              memory loads the indices and values from global memory into registers
-                              (one 256-nonzero step ahead) instead of staging them in shared memory;
-                              0 = staged */
 } spmv_plan_opts;
 
 /* Summary of a plan (spmv_plan_info). */

@@ -70,9 +70,9 @@ def spmv_plan(m, n, nnz, layout, ptr, idx, vals, val_dtype, vec_dtype, stream=No
 
 
 def spmv_plan_ex(m, n, nnz, layout, ptr, idx, vals, val_dtype, vec_dtype, stream=None, flags=0, chunks=0,
-                 warps_per_cta=0, tile_items=0, stages=0, chunk_tiles=0, scatter_loads=0):
+                 warps_per_cta=0, tile_items=0, stages=0, chunk_tiles=0):
     h = ctypes.c_void_p()
-    opts = _lib.spmv_plan_opts(chunks, warps_per_cta, tile_items, stages, chunk_tiles, scatter_loads)
+    opts = _lib.spmv_plan_opts(chunks, warps_per_cta, tile_items, stages, chunk_tiles)
     _lib.call("spmv_plan_ex", ctypes.byref(h), m, n, nnz, layout, _addr(ptr), _addr(idx), _addr(vals), val_dtype,
               vec_dtype, _stream(stream), flags, ctypes.byref(opts))
     return h.value
@@ -223,7 +223,7 @@ class Plan:
     """Plan over torch device tensors ``ptr``/``idx``/``vals`` (CSC for layout "csc", CSR for "csr")."""
 
     def __init__(self, m, n, ptr, idx, vals, layout="csc", vec_dtype=None, flags=0, chunks=0, warps_per_cta=0,
-                 tile_items=0, stages=0, stream=None, chunk_tiles=0, scatter_loads=0):
+                 tile_items=0, stages=0, stream=None, chunk_tiles=0):
         import torch
 
         self.m, self.n = int(m), int(n)
@@ -236,7 +236,7 @@ class Plan:
         self.nnz = int(idx.numel())
         self.handle = spmv_plan_ex(self.m, self.n, self.nnz, self.layout, ptr, idx, vals, dtype_code(vals.dtype),
                                    dtype_code(vec_dtype), stream, flags, chunks, warps_per_cta, tile_items, stages,
-                                   chunk_tiles, scatter_loads)
+                                   chunk_tiles)
 
     @classmethod
     def from_matrix(cls, A, **kw):

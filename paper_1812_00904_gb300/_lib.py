@@ -38,7 +38,7 @@ class SpmvError(RuntimeError):
 
 class spmv_plan_opts(ctypes.Structure):
     _fields_ = [("chunks", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32), ("tile_items", ctypes.c_int32),
-                ("stages", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32), ("scatter_loads", ctypes.c_int32)]
+                ("stages", ctypes.c_int32), ("chunk_tiles", ctypes.c_int32)]
 
 
 class spmv_plan_info_t(ctypes.Structure):

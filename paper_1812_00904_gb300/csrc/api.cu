@@ -112,13 +112,8 @@ struct SlotGeom {
 };
 SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     SlotGeom g;
-    if (mode == MODE_SCATTER_G) {  // indices and values are not staged
-        g.off_val = 0;
-        g.off_mask = 0;
-    } else {
-        g.off_val = (int)align_up((size_t)p->T * 4, 128);
-        g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
-    }
+    g.off_val = (int)align_up((size_t)p->T * 4, 128);
+    g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
     g.off_x = g.off_mask + (int)align_up((size_t)p->mwp * 4, 16);
     const int nx = mode == MODE_SEGDOT ? 0 : mode == MODE_DVALUES ? 1 : kbt;
     g.off_hdr = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 16);  // 32-byte tile header
@@ -128,7 +123,7 @@ SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
 // On-chip short-vector bytes of a pass (accumulator of the scatter mode, input otherwise).
 size_t vec_bytes(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
     if (!smemv) return 0;
-    const size_t e = (mode == MODE_SCATTER || mode == MODE_SCATTER_G) ? (size_t)p->sa : (size_t)p->sx;
+    const size_t e = mode == MODE_SCATTER ? (size_t)p->sa : (size_t)p->sx;
     return align_up((size_t)p->n_minor * kbt * e, 128);
 }
 // Warps per CTA of a pass: the plan's warps, as many as the shared memory holds.
@@ -137,10 +132,7 @@ int warps_for(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
     const SlotGeom g = slot_geom(p, mode, kbt);
     const size_t room = (size_t)p->smem_max > vec + BAR_BYTES ? (size_t)p->smem_max - vec - BAR_BYTES : 0;
     const int fit = (int)std::min<size_t>(room / ((size_t)p->S * g.bytes), 64);
-    // the register-load scatter pass keeps its prefetched step in registers: at most the warps
-    // that may use 128 registers a thread
-    const int cap = (kbt > 1 || mode == MODE_SCATTER_G) ? MAX_WARPS_KB : MAX_WARPS;
-    const int w = std::min({p->W, cap, fit});
+    const int w = std::min({p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
     // one warp beyond WARPS_REGS costs the others their larger register budget: not worth it
     return w == WARPS_REGS + 1 ? WARPS_REGS : w;
 }
@@ -210,15 +202,13 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     a.sp = base_params(p);
     a.sp.kb = kb;
     for (int b = 0; b < kb; ++b) a.sp.vin[b] = in[b];
-    // one vector on chip: indices and values loaded into registers when the plan asks for it
-    const int mode = (p->scatter_loads && kb == 1 && p->onchip) ? MODE_SCATTER_G : MODE_SCATTER;
-    set_geometry(p, a, mode, kb_template(kb), p->onchip);
+    set_geometry(p, a, MODE_SCATTER, kb_template(kb), p->onchip);
     a.sp.part = p->part;
     if (!p->onchip) CUDA_TRY(cudaMemsetAsync(p->part, 0, (size_t)p->n_minor * sizeof(double), s));
     a.stream = s;
     {
         ProfScope ps(p, 0, s);
-        CUDA_TRY(launch_stream(p, mode, kb, a));
+        CUDA_TRY(launch_stream(p, MODE_SCATTER, kb, a));
     }
     {
         ProfScope ps(p, 1, s);
@@ -647,7 +637,6 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     const int nt = p->ntiles;
     p->ctas = (pi && pi->ctas > 0) ? std::min(pi->ctas, std::max(nt, 1)) : std::max(1, std::min(sms, nt));
     p->chunk_tiles = (opts && opts->chunk_tiles > 0) ? opts->chunk_tiles : CHUNK_TILES;
-    p->scatter_loads = (opts && opts->scatter_loads) ? 1 : 0;
     // processors (chunks of tiles) of the streaming passes and their nonzero boundaries
     std::vector<int32_t> pnzb;
     {

@@ -78,30 +78,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-// Streaming global loads (read once: no L1 allocation).
-__device__ __forceinline__ int32_t ld_stream(const int32_t *p) {
-    int32_t v;
-    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ float ld_stream(const float *p) {
-    float v;
-    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-__device__ __forceinline__ double ld_stream(const double *p) {
-    double v;
-    asm volatile("ld.global.nc.L1::no_allocate.f64 %0, [%1];" : "=d"(v) : "l"(p));
-    return v;
-}
-template <typename T> __device__ __forceinline__ T ld_stream(const T *p) {  // 2-byte values
-    unsigned short u;
-    asm volatile("ld.global.nc.L1::no_allocate.b16 %0, [%1];" : "=h"(u) : "l"(p));
-    T v;
-    memcpy(&v, &u, 2);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
 // element types
 

@@ -6,9 +6,6 @@ namespace gbk {
 cudaError_t launch_stream_bf16(int mode, int kb, const LaunchArgs &a) {
     using VT = __nv_bfloat16;
     using XT = float;
-    if (mode == MODE_SCATTER_G) {
-        return (a.smemv && kb == 1) ? launch_one<VT, XT, MODE_SCATTER_G, 1, true>(a) : cudaErrorInvalidValue;
-    }
     if (mode == MODE_DVALUES) {
         return a.smemv ? launch_one<VT, XT, MODE_DVALUES, 1, true>(a) : launch_one<VT, XT, MODE_DVALUES, 1, false>(a);
     }

@@ -15,7 +15,6 @@ enum Mode : int {
     MODE_SCATTER = 0,  // acc[idx[k]] += val[k] * w[major(k)]   (CSC A x, CSR v^T A)
     MODE_SEGDOT = 1,   // out[j] = sum_{k in segment j} val[k] * w[idx[k]]   (CSC v^T A, CSR A x)
     MODE_DVALUES = 2,  // g[k] = minor[idx[k]] * major[seg(k)]
-    MODE_SCATTER_G = 3,  // MODE_SCATTER with indices and values loaded from global memory into registers
 };
 
 constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels

@@ -28,7 +28,6 @@ struct spmv_plan_s {
     int W_info = 0;                       // warps of the single-vector scatter pass (spmv_plan_info)
     int mwp = 0, x_cap = 0, pptr_len = 0, smem_max = 0;  // masks words per tile, window elements per tile
     int chunk_tiles = 1;  // tiles per chunk of the streaming kernels' full rounds
-    int scatter_loads = 0;  // 1: the single-vector scatter pass loads indices and values into registers
     bool onchip = false;
     int batch_width = 1;
 

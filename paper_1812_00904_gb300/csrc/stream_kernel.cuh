@@ -31,10 +31,6 @@
 //                 their partial sums in the chunk's carry records for the zone
 //                 fixup.
 //   MODE_DVALUES: g[k] = minor[idx[k]] * major[seg(k)].
-//   MODE_SCATTER_G: MODE_SCATTER, with the indices and values read from global
-//                 memory into registers one 256-position step ahead instead of
-//                 staged in shared memory (the shared-memory pipe then carries
-//                 the atomic additions alone, besides the small per-tile copies).
 #pragma once
 
 #include "device_common.cuh"
@@ -98,7 +94,6 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
-    constexpr bool SCAT = MODE == MODE_SCATTER || MODE == MODE_SCATTER_G;
     const int kb = (MODE == MODE_DVALUES) ? 1 : p.kb;
     const int nvec = (MODE == MODE_DVALUES) ? 1 : p.kb;
     const int S = p.slots;
@@ -219,8 +214,6 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         if (lane == 2) {
             e0 = e.y * p.mwp;
             cnt = p.mwp;
-        } else if (MODE == MODE_SCATTER_G && lane < 2) {
-            cnt = 0;  // indices and values come straight from global memory
         } else if (lane >= 3) {
             e0 = xbase;
             cnt = (c_x && nxc <= p.x_cap) ? nxc : 0;
@@ -253,7 +246,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
 
     // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES)
     if constexpr (SMEMV) {
-        if constexpr (SCAT) {
+        if constexpr (MODE == MODE_SCATTER) {
             AT *acc = reinterpret_cast<AT *>(smem);
             for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
         } else {
@@ -305,33 +298,6 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     bool cleft = false;
     // first element of this CTA's window of the input vector (SEGDOT over row-sorted blocks)
     const int vwin = (MODE == MODE_SEGDOT && p.win) ? p.win[blockIdx.x].x : 0;
-
-    // MODE_SCATTER_G: indices and values of the next 256-position step, in registers
-    int prow[8];
-    VT pval[8];
-    auto gfetch = [&](int kb0, int s0, int rel_lo, int rel_hi) {
-        if constexpr (MODE == MODE_SCATTER_G) {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int pos = s0 + (e << 5) + lane;
-                if (pos >= rel_lo && pos < rel_hi) {
-                    prow[e] = ld_stream(p.idx + kb0 + pos);
-                    pval[e] = ld_stream(static_cast<const VT *>(p.vals) + kb0 + pos);
-                } else {
-                    prow[e] = 0;
-                    pval[e] = VT(0);
-                }
-            }
-        }
-    };
-    if constexpr (MODE == MODE_SCATTER_G) {
-        if (nk > 0) {
-            int4 d, e;
-            desc(0, d, e);
-            const int kb0 = d.x & ~7;
-            gfetch(kb0, 0, d.x - kb0, d.w - kb0);
-        }
-    }
 
     // running sum of the open segment (SEGDOT): compensated (hi + lo) in the accumulation
     // type, carried from one of this warp's tiles into the next while the segment runs on
@@ -593,36 +559,16 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         int row[8];
                         AT a[8];
                         uint32_t ok = 0xFFu;
-                        if constexpr (MODE == MODE_SCATTER_G) {
-                            // this step's values arrived in registers; fetch the next step's (this
-                            // tile's, or the first of the warp's next tile) before the additions
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int pos = s0 + (e << 5) + lane;
-                                row[e] = prow[e];
-                                a[e] = to_acc<AT>(pval[e]);
-                                if (!(WHOLE || (pos >= rel_lo && pos < rel_hi))) ok &= ~(1u << e);
-                            }
-                            if (stp + 1 < nsteps) {
-                                gfetch(kb0, s0 + 256, rel_lo, rel_hi);
-                            } else if (k + 1 < nk) {
-                                int4 dn, en;
-                                desc(k + 1, dn, en);
-                                const int nkb0 = dn.x & ~7;
-                                gfetch(nkb0, 0, dn.x - nkb0, dn.w - nkb0);
-                            }
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int pos = s0 + (e << 5) + lane;
-                                if (WHOLE || (pos >= rel_lo && pos < rel_hi)) {
-                                    row[e] = idx_s[pos];
-                                    a[e] = to_acc<AT>(vv[pos]);
-                                } else {
-                                    row[e] = 0;
-                                    a[e] = AT(0);
-                                    ok &= ~(1u << e);
-                                }
+                        for (int e = 0; e < 8; ++e) {
+                            const int pos = s0 + (e << 5) + lane;
+                            if (WHOLE || (pos >= rel_lo && pos < rel_hi)) {
+                                row[e] = idx_s[pos];
+                                a[e] = to_acc<AT>(vv[pos]);
+                            } else {
+                                row[e] = 0;
+                                a[e] = AT(0);
+                                ok &= ~(1u << e);
                             }
                         }
                         if constexpr (CHECK) {
@@ -847,7 +793,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             clo[b] = AT(0);
                         }
                     }
-                } else if constexpr (SCAT) {
+                } else if constexpr (MODE == MODE_SCATTER) {
                     if (win && full && !dup && !p.checked)
                         run_scatter(BoolC<true>{}, BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
                     else if (win)
@@ -881,7 +827,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         }
     }
 
-    if constexpr (SCAT && SMEMV) {
+    if constexpr (MODE == MODE_SCATTER && SMEMV) {
         __syncthreads();
         const AT *acc = reinterpret_cast<const AT *>(smem);
         AT *part = static_cast<AT *>(p.part);

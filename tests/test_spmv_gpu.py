@@ -396,33 +396,3 @@ def test_kernel_timers_count_launches_and_switch_on_and_off():
     assert pkg.spmv_profile_read(quiet.handle, 0)[1] == 1
     plan.check()
     quiet.check()
-
-
-@pytest.mark.parametrize("layout", ["csc", "csr"])
-@pytest.mark.parametrize("dtype", DTYPES, ids=str)
-@pytest.mark.parametrize("shape,tile", [((500, 40_000), 0), ((2000, 3), 0), ((300, 60_000), 64), ((37, 2000), 0)])
-def test_scatter_register_loads_match_oracle(layout, dtype, shape, tile):
-    """The scatter pass that loads indices and values into registers (plan option scatter_loads),
-    with whole and partial tiles, empty segments and duplicates, against the oracle."""
-    m, n = shape if layout == "csc" else shape[::-1]
-    A = synth.random_matrix(m, n, layout, density=min(0.05, 40.0 / max(1, min(m, n)) + 0.01), seed=m + n + 3,
-                            duplicates=True)
-    plan, stored = make_plan(A, dtype, scatter_loads=1, tile_items=tile)
-    check_products(plan, stored, synth.uniform_vector(n, 5), synth.uniform_vector(m, 6), TOL[dtype],
-                   f"register loads {layout} {dtype} {shape}")
-    plan.close()
-
-
-def test_scatter_register_loads_unvalidated_indices_are_reported():
-    """With validation skipped, an index outside the short vector is clamped and reported."""
-    A = synth.random_matrix(300, 20_000, "csc", density=0.02, seed=77)
-    idx = np.asarray(A.idx, np.int32).copy()
-    idx[::501] = A.m + 3
-    t = dict(ptr=torch.from_numpy(np.asarray(A.ptr, np.int32)).to(DEV), idx=torch.from_numpy(idx).to(DEV),
-             vals=torch.from_numpy(np.asarray(A.vals, np.float32)).to(DEV))
-    plan = pkg.Plan(A.m, A.n, t["ptr"], t["idx"], t["vals"], flags=pkg.SPMV_PLAN_NO_VALIDATE, scatter_loads=1)
-    plan.spmv(dev_vec(synth.uniform_vector(A.n, 1), torch.float32))
-    with pytest.raises(pkg.SpmvError) as e:
-        plan.check()
-    assert e.value.status == pkg._lib.SPMV_ERR_DEVICE
-    plan.close()
