@@ -100,6 +100,7 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.rec_left = p->rec_left;
     sp.rec_right = p->rec_right;
     sp.chunk_tiles = p->chunk_tiles;
+    sp.blocks_per_cta = p->bpc;
     sp.win = p->win;
     sp.err = p->err;
     return sp;
@@ -636,14 +637,15 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     // ---- workspace, part 2: tiles (descriptors, masks), processor zones, records and partial sums
     const int nt = p->ntiles;
     p->ctas = (pi && pi->ctas > 0) ? std::min(pi->ctas, std::max(nt, 1)) : std::max(1, std::min(sms, nt));
+    p->bpc = (pi && pi->blocks_per_cta > 1 && (int64_t)p->ctas * pi->blocks_per_cta <= nt) ? pi->blocks_per_cta : 1;
     p->chunk_tiles = (opts && opts->chunk_tiles > 0) ? opts->chunk_tiles : CHUNK_TILES;
     // processors (chunks of tiles) of the streaming passes and their nonzero boundaries
     std::vector<int32_t> pnzb;
     {
         spmv_plan_s::ProcZones &pz = p->pz;
-        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas, p->chunk_tiles, nullptr);
+        pz.nproc = stream_processors(nt, p->T, (int)nnz, p->ctas * p->bpc, p->chunk_tiles, nullptr);
         pnzb.resize((size_t)pz.nproc + 1);
-        stream_processors(nt, p->T, (int)nnz, p->ctas, p->chunk_tiles, pnzb.data());
+        stream_processors(nt, p->T, (int)nnz, p->ctas * p->bpc, p->chunk_tiles, pnzb.data());
         p->max_nproc = std::max(1, pz.nproc);
     }
     const size_t part_bytes = (pi && pi->segdot_only) ? 16

@@ -10,11 +10,12 @@
 // by their short-vector index (row of a wide matrix), so the block's
 // contribution to y_i is the dot product of its row-i nonzeros with the
 // block's window of x -- the segmented pass of Sec. IV-A over segments
-// (block, row), reading x from a shared-memory copy of the block's window.
+// (block, row), reading x from a shared-memory copy of the block's window; each
+// CTA runs G / (SM count) blocks in turn, restaging the window between them.
 // The per-block short vectors are then added in FP64 in block order (Sec. III
 // step 2).  The copy is laid out as a CSR matrix with G * m rows (segment g * m + i
 // = row i of block g) whose column indices are offsets into the block's
-// window, and planned like any other matrix, with one CTA per block.
+// window, and planned like any other matrix with its tiles cut into the G blocks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -200,9 +201,11 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     cudaMemcpy(&e, p->err, 4, cudaMemcpyDeviceToHost);
     if (e) return set_error(SPMV_ERR_DEVICE, "row blocks: index out of range while sorting");
 
-    // ---- the copy as a CSR matrix of G * m rows over windows of wmax columns, one CTA per block
+    // ---- the copy as a CSR matrix of G * m rows over windows of wmax columns; one CTA per SM runs
+    // G / sms blocks in turn, restaging the window between them
     PlanInternal pi;
-    pi.ctas = G;
+    pi.ctas = sms;
+    pi.blocks_per_cta = G / sms;
     pi.segdot_only = true;
     spmv_plan_opts o{};
     o.tile_items = T;
@@ -213,7 +216,7 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
     st = plan_create(&q, (int64_t)nseg, wmax, p->nnz, SPMV_CSR_TALL, bptr, sidx, svals, p->val_t, p->vec_t, s,
                      p->flags & SPMV_PLAN_BANK_ORDER, &o, &pi);
     if (st != SPMV_OK) return st;
-    if (!q->onchip || q->ctas != G) {  // the windows must sit in shared memory, one block per CTA
+    if (!q->onchip || q->ctas * q->bpc != G) {  // the windows must sit in shared memory, block by block
         plan_free(q);
         return SPMV_OK;
     }

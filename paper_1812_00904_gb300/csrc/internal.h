@@ -69,7 +69,8 @@ struct StreamParams {
     void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
     void *rec_left, *rec_right;  // SEGDOT carry records [b * nproc + proc]: (hi, lo) pairs of the accumulation type
     int32_t nproc;           // processors (chunks of tiles) of the plan: the record stride
-    int32_t chunk_tiles;     // C, tiles per chunk (before the single-tile tail of every CTA)
+    int32_t chunk_tiles;     // C, tiles per chunk (before the single-tile tail of every block)
+    int32_t blocks_per_cta;  // BPC: the tiles form gridDim.x BPC blocks; a CTA runs BPC of them in turn
     const int2 *win;         // SEGDOT over row-sorted blocks: per CTA (first element, length) of its window of
                              // the input vector; the indices are offsets into the window (NULL: whole vector)
     int32_t *err;

@@ -28,6 +28,7 @@ struct spmv_plan_s {
     int W_info = 0;                       // warps of the single-vector scatter pass (spmv_plan_info)
     int mwp = 0, x_cap = 0, pptr_len = 0, smem_max = 0;  // masks words per tile, window elements per tile
     int chunk_tiles = 1;  // tiles per chunk of the streaming kernels' full rounds
+    int bpc = 1;          // blocks (Sec. II ranges of whole tiles) each CTA runs in turn
     bool onchip = false;
     int batch_width = 1;
 
@@ -97,6 +98,7 @@ namespace gbk {
 // Internal overrides of a plan made by the library itself.
 struct PlanInternal {
     int ctas = 0;             // CTAs of every pass (0: one per SM, at most one per tile)
+    int blocks_per_cta = 1;   // blocks of tiles each CTA runs in turn
     bool segdot_only = false; // only single-vector segmented passes will run
 };
 spmv_status plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nnz, int32_t layout, const int32_t *ptr,

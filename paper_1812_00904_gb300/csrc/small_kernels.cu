@@ -19,6 +19,20 @@ struct InPtrs {
     const void *p[KB_MAX];
 };
 
+// An FP32 value widened to FP64 exactly.  Normal numbers by moving the sign, exponent
+// (rebiased from 127 to 1023) and mantissa bits with integer operations, which leaves the
+// FP64 pipe (slow on this part) to the additions; zeros, subnormals, infinities and NaNs by
+// the converting instruction.
+__device__ __forceinline__ double widen(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return static_cast<double>(f);
+    const uint64_t d = (static_cast<uint64_t>(u & 0x80000000u) << 32) | (static_cast<uint64_t>(e + 896u) << 52) |
+                       (static_cast<uint64_t>(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double(static_cast<long long>(d));
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
 // out_b[i] = sum_{q < nparts} part[q * qstride + b * bstride + i].  A block takes 32
 // consecutive elements; its 8 thread rows sum the partials q = row, row + 8, ... in
 // FP64 and the 8 row sums are added in row order: a fixed order, independent of
@@ -35,7 +49,7 @@ __global__ void __launch_bounds__(COMB_X * COMB_Y) combine_kernel(const PT *__re
     if (i < n_minor) {
         const PT *src = part + (size_t)b * bstride + i;
 #pragma unroll 4
-        for (int q = row; q < nparts; q += COMB_Y) s += static_cast<double>(__ldg(src + (size_t)q * qstride));
+        for (int q = row; q < nparts; q += COMB_Y) s += widen(__ldg(src + (size_t)q * qstride));
     }
     sh_s[row][threadIdx.x] = s;
     __syncthreads();
@@ -64,7 +78,7 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
         const RT *rr = rec_right + (size_t)b * P;
         const RT l = rec_left[(size_t)b * P + zd.last];
         // hi and lo parts summed apart in FP64 (for FP32 records both widen exactly)
-        double sh = static_cast<double>(rr[zd.first].x), sl = static_cast<double>(rr[zd.first].y);
+        double sh = widen(rr[zd.first].x), sl = widen(rr[zd.first].y);
         int q = zd.first + 1;
         for (; q + 8 <= zd.last; q += 8) {
             RT m[8];
@@ -72,16 +86,16 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
             for (int e = 0; e < 8; ++e) m[e] = rr[q + e];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                sh += static_cast<double>(m[e].x);
-                sl += static_cast<double>(m[e].y);
+                sh += widen(m[e].x);
+                sl += widen(m[e].y);
             }
         }
         for (; q < zd.last; ++q) {
-            sh += static_cast<double>(rr[q].x);
-            sl += static_cast<double>(rr[q].y);
+            sh += widen(rr[q].x);
+            sl += widen(rr[q].y);
         }
-        sh += static_cast<double>(l.x);
-        sl += static_cast<double>(l.y);
+        sh += widen(l.x);
+        sl += widen(l.y);
         const double s = sh + sl;
         static_cast<XT *>(out.p[b])[zd.col] = static_cast<XT>(s);
     }

@@ -102,25 +102,32 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     uint64_t *myfull = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes) + warp * S;
     unsigned char *myslots = smem + p.vec_region_bytes + BAR_BYTES + (size_t)warp * S * p.slot_bytes;
 
-    // this CTA's tiles [ta, ta + nct): the Sec. II rule over the grid; nb chunks of C tiles,
-    // then nct - nb C single-tile chunks
-    const int G = gridDim.x, g = blockIdx.x;
-    const int tq = p.ntiles / G, tr = p.ntiles % G;
-    const int ta = g * tq + min(g, tr);
-    const int nct = tq + (g < tr ? 1 : 0);
+    // Blocks: the grid's G BPC consecutive ranges of whole tiles, equal by the Sec. II rule
+    // (BPC = 1 but for the windowed pass over row-sorted blocks); this CTA runs blocks
+    // BPC g .. BPC g + BPC - 1 one after the other.  A block's tiles [ta, ta + nct) form nb
+    // chunks of C tiles and then nct - nb C single-tile chunks.
+    const int BPC = p.blocks_per_cta;
+    const int GB = gridDim.x * BPC;
+    const int tq = p.ntiles / GB, tr = p.ntiles % GB;
     const int C = p.chunk_tiles;
     auto big_chunks = [&](int n) { return (n - min(n, MAX_WARPS * C + MAX_WARPS)) / C; };
-    const int nb = big_chunks(nct);
-    const int cnt = nb / W + (warp < nb % W ? 1 : 0);    // C-tile chunks of this warp
-    const int nk = nct / W + (warp < nct % W ? 1 : 0);   // tiles of this warp
-    // first tail tile of this warp: the tiles of the warps before it less their C-tile chunks
-    const int toff = (warp * (nct / W) + min(warp, nct % W)) - C * (warp * (nb / W) + min(warp, nb % W));
-    auto tile_of = [&](int k) {  // tile of this warp's k-th tile
+    // processors (chunks) before a block: a block of n tiles has big_chunks(n) + n - C big_chunks(n)
+    auto chunks_of = [&](int n) { return n - (C - 1) * big_chunks(n); };
+    int gb = 0, ta = 0, nb = 0, cnt = 0, nk = 0, toff = 0, chunk0 = 0;
+    auto enter_block = [&](int hb) {
+        gb = blockIdx.x * BPC + hb;
+        ta = gb * tq + min(gb, tr);
+        const int nct = tq + (gb < tr ? 1 : 0);
+        nb = big_chunks(nct);
+        cnt = nb / W + (warp < nb % W ? 1 : 0);   // C-tile chunks of this warp
+        nk = nct / W + (warp < nct % W ? 1 : 0);  // tiles of this warp
+        // first tail tile of this warp: the tiles of the warps before it less their C-tile chunks
+        toff = (warp * (nct / W) + min(warp, nct % W)) - C * (warp * (nb / W) + min(warp, nb % W));
+        chunk0 = gb * chunks_of(tq) + min(gb, tr) * (chunks_of(tq + 1) - chunks_of(tq));
+    };
+    auto tile_of = [&](int k) {  // tile of this warp's k-th tile of the block
         return k < cnt * C ? ta + (warp + (k / C) * W) * C + k % C : ta + nb * C + toff + (k - cnt * C);
     };
-    // processors (chunks) before this CTA: a CTA of n tiles has big_chunks(n) + n - C big_chunks(n)
-    auto chunks_of = [&](int n) { return n - (C - 1) * big_chunks(n); };
-    const int chunk0 = g * chunks_of(tq) + min(g, tr) * (chunks_of(tq + 1) - chunks_of(tq));
 
     // this warp's slot barriers (used by this warp only)
     if (lane == 0) {
@@ -151,8 +158,6 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         }
     };
     int cb = 0;  // batch held in dcur
-    load_batch(0, dcur, ecur);
-    load_batch(1, dnxt, enxt);
     // descriptor of this warp's tile k (its batch is cb or cb + 1)
     auto desc = [&](int k, int4 &d, int4 &e) {
         const bool c = (k >> 5) == cb;
@@ -242,33 +247,31 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         if (bytes) bulk_g2s(dst, c_src + (size_t)e0 * c_es, bytes, &myfull[s]);
     };
 
-    for (int k = 0; k < min(S, nk); ++k) issue(k, k);  // the first copies fly while the vector is staged
-
-    // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES)
-    if constexpr (SMEMV) {
-        if constexpr (MODE == MODE_SCATTER) {
-            AT *acc = reinterpret_cast<AT *>(smem);
-            for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
-        } else {
-            // the input vector, or this CTA's window of it (row-sorted blocks; its first
-            // element is 16-byte aligned)
+    // ---- the short (minor) vector on chip: accumulator (SCATTER) or input (SEGDOT / DVALUES):
+    // the whole vector, or block gbk's window of it (row-sorted blocks; its first element is
+    // 16-byte aligned).  Called by all threads; one vector goes by bulk copies on the barrier
+    // sbar, whose phases sphase counts.
+    uint64_t *sbar = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes + BAR_BYTES) - 1;
+    uint32_t sphase = 0;
+    if (SMEMV && MODE != MODE_SCATTER && KB == 1 && threadIdx.x == 0) {
+        mbar_init(sbar, 1);
+        fence_mbar_init();
+    }
+    auto stage_vector = [&](int gbk) {
+        if constexpr (SMEMV && MODE != MODE_SCATTER) {
             XT *vs = reinterpret_cast<XT *>(smem);
             int wb = 0, wl = p.n_minor;
             if (MODE == MODE_SEGDOT && p.win) {
-                const int2 w = p.win[blockIdx.x];
+                const int2 w = p.win[gbk];
                 wb = w.x;
                 wl = min(w.y, p.n_minor);
             }
             if constexpr (KB == 1) {
-                // one vector: its 16-byte aligned part by bulk copies on one barrier, the rest
-                // (under 16 bytes) by plain loads
+                // its 16-byte aligned part by bulk copies, the rest (under 16 bytes) by plain loads
                 const XT *src = static_cast<const XT *>(p.vin[0]) + wb;
                 constexpr int xa = 16 / (int)sizeof(XT);
                 const int wbulk = wl & ~(xa - 1);
-                uint64_t *sbar = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes + BAR_BYTES) - 1;
                 if (threadIdx.x == 0 && wbulk > 0) {
-                    mbar_init(sbar, 1);
-                    fence_mbar_init();
                     mbar_arrive_expect_tx(sbar, static_cast<uint32_t>(wbulk) * (uint32_t)sizeof(XT));
                     constexpr int piece = 32768 / (int)sizeof(XT);
                     for (int o = 0; o < wbulk; o += piece)
@@ -277,9 +280,12 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 }
                 for (int i = wbulk + threadIdx.x; i < wl; i += blockDim.x) vs[i] = src[i];
                 __syncthreads();  // the barrier's initialisation before anyone waits on it
-                if (wbulk > 0 && !mbar_wait_bounded(sbar, 0, WAIT_LIMIT_NS)) {
-                    if (threadIdx.x == 0) atomicOr(p.err, ERR_WAIT);
-                    mbar_wait_bounded(sbar, 0, WAIT_LIMIT_NS);  // let the copy land before going on
+                if (wbulk > 0) {
+                    if (!mbar_wait_bounded(sbar, sphase & 1u, WAIT_LIMIT_NS)) {
+                        if (threadIdx.x == 0) atomicOr(p.err, ERR_WAIT);
+                        mbar_wait_bounded(sbar, sphase & 1u, WAIT_LIMIT_NS);  // let the copy land first
+                    }
+                    ++sphase;
                 }
             } else {
                 for (int i = threadIdx.x; i < wl; i += blockDim.x) {
@@ -289,28 +295,47 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 }
             }
         }
+    };
+    if constexpr (SMEMV && MODE == MODE_SCATTER) {
+        AT *acc = reinterpret_cast<AT *>(smem);
+        for (int i = threadIdx.x; i < p.n_minor * KB; i += blockDim.x) acc[i] = AT(0);
     }
-    __syncthreads();
 
     // the open segment at the start of the current chunk: its first segment, and whether that
     // began in the previous chunk (then its sum goes to the chunk's left record)
     int cfirst = -1;
     bool cleft = false;
-    // first element of this CTA's window of the input vector (SEGDOT over row-sorted blocks)
-    const int vwin = (MODE == MODE_SEGDOT && p.win) ? p.win[blockIdx.x].x : 0;
-
+    // first element of the current block's window of the input vector (row-sorted blocks)
+    int vwin = 0;
     // running sum of the open segment (SEGDOT): compensated (hi + lo) in the accumulation
     // type, carried from one of this warp's tiles into the next while the segment runs on
     AT chi[KB], clo[KB];
+
+    int s = 0;        // slot of the warp's next tile to consume
+    uint32_t ph = 0;  // phase parity of that slot's barrier
+    bool wfail = false;  // a staging wait of this warp timed out: it does no more work
+    for (int hb = 0; hb < BPC; ++hb) {
+    enter_block(hb);
+    cb = 0;
+    load_batch(0, dcur, ecur);
+    load_batch(1, dnxt, enxt);
+    if (!wfail)
+        for (int k = 0; k < min(S, nk); ++k) issue(k, (s + k) % S);  // the first copies fly while the vector is staged
+    if (hb == 0 || p.win) {
+        if (hb > 0) __syncthreads();  // every warp is done with the previous block's window
+        stage_vector(gb);
+    }
+    __syncthreads();
+    cfirst = -1;
+    cleft = false;
+    vwin = (MODE == MODE_SEGDOT && p.win) ? p.win[gb].x : 0;
 #pragma unroll
     for (int b = 0; b < KB; ++b) {
         chi[b] = AT(0);
         clo[b] = AT(0);
     }
 
-    int s = 0;        // slot of tile k
-    uint32_t ph = 0;  // phase parity of that slot's barrier
-    for (int k = 0; k < nk; ++k) {
+    for (int k = 0; k < nk && !wfail; ++k) {
         unsigned char *slot = myslots + (size_t)s * p.slot_bytes;
         bool ok = mbar_wait_bounded(&myfull[s], ph, WAIT_LIMIT_NS);
         ok = __all_sync(FULL, ok);
@@ -321,6 +346,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 const int qs = s + q < S ? s + q : s + q - S;
                 mbar_wait_bounded(&myfull[qs], s + q < S ? ph : ph ^ 1u, WAIT_LIMIT_NS);
             }
+            wfail = true;
             break;
         }
         // tile header: first nonzero, first owned end event, flags, next tile's first
@@ -826,6 +852,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
             ph ^= 1u;
         }
     }
+
+    }  // blocks of this CTA
 
     if constexpr (MODE == MODE_SCATTER && SMEMV) {
         __syncthreads();
