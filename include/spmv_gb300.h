@@ -286,8 +286,7 @@ spmv_status spmv_profile_enable(spmv_plan_t plan, int32_t on);
  * library until the process exits.  All calls share it, so calls that
  * overlap on the GPU race and give wrong results; serialize them (one stream,
  * or events).  The first call on a device resolves the array's device address
- * (set-up), so make that first call before any stream capture.  Nothing is
- * allocated; an m above 49152 or a bad size is rejected with
+ * (a host-side query, once per device).  Nothing is allocated; an m above 49152 or a bad size is rejected with
  * SPMV_ERR_INVALID_ARG before any launch.  The matrix is not validated and
  * device-side problems are not reported (there is no error word to read back):
  * a nonzero whose row index lies outside [0, m) is skipped, and a malformed ptr
