@@ -116,13 +116,15 @@ SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     g.off_val = (int)align_up((size_t)p->T * 4, 128);
     g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
     g.off_x = g.off_mask + (int)align_up((size_t)p->mwp * 4, 16);
-    const int nx = mode == MODE_SEGDOT ? 0 : mode == MODE_DVALUES ? 1 : kbt;
+    const int nx = (mode == MODE_SEGDOT || mode == MODE_VSEG) ? 0 : mode == MODE_DVALUES ? 1 : kbt;
     g.off_hdr = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 16);  // 32-byte tile header
     g.bytes = (int)align_up((size_t)g.off_hdr + 32, 128);
     return g;
 }
 // On-chip short-vector bytes of a pass (accumulator of the scatter mode, input otherwise).
 size_t vec_bytes(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
+    if (mode == MODE_VSEG)  // 8 values of scratch per lane, then the interleaved vectors when on chip
+        return (size_t)WARPS_VSEG * 32 * 8 * 4 + (smemv ? align_up((size_t)p->n_minor * kbt * p->sx, 128) : 0);
     if (!smemv) return 0;
     const size_t e = mode == MODE_SCATTER ? (size_t)p->sa : (size_t)p->sx;
     return align_up((size_t)p->n_minor * kbt * e, 128);
@@ -133,7 +135,7 @@ int warps_for(const spmv_plan_s *p, int mode, int kbt, bool smemv) {
     const SlotGeom g = slot_geom(p, mode, kbt);
     const size_t room = (size_t)p->smem_max > vec + BAR_BYTES ? (size_t)p->smem_max - vec - BAR_BYTES : 0;
     const int fit = (int)std::min<size_t>(room / ((size_t)p->S * g.bytes), 64);
-    const int w = std::min({p->W, kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
+    const int w = std::min({p->W, mode == MODE_VSEG ? WARPS_VSEG : kbt > 1 ? MAX_WARPS_KB : MAX_WARPS, fit});
     // one warp beyond WARPS_REGS costs the others their larger register budget: not worth it
     return w == WARPS_REGS + 1 ? WARPS_REGS : w;
 }
@@ -219,14 +221,11 @@ spmv_status run_scatter(spmv_plan_s *p, int kb, const void *const *in, void *con
     return SPMV_OK;
 }
 
-// 2..KB_MAX vectors of a segmented pass read from global memory, interleaved into the plan's
-// buffer vt (in_len entries each): every nonzero fetches its index's kb entries with one or two
-// vector loads (through L2), so the matrix streams once for all of them.
-static spmv_status run_segdot_global(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
-                                     spmv_plan_s *prof, int id_dot, int id_fix, int64_t in_len) {
-    const int kbt = kb_template(kb);
-    const int64_t len = in_len >= 0 ? in_len : p->n_minor;
-    const size_t need = (size_t)std::max<int64_t>(len, 1) * KB_MAX * p->sx;
+// The plan's buffer vt holding kb input vectors interleaved with stride kbt (in_len entries
+// each: the short vector, or the long vector of a row-sorted copy's windows).
+static spmv_status interleave_inputs(spmv_plan_s *p, int kbt, int kb, const void *const *in, int64_t len,
+                                     cudaStream_t s) {
+    const size_t need = (size_t)std::max<int64_t>(len, 1) * std::max(KB_MAX, VL_MAX) * p->sx;
     if (p->vt_bytes < need) {
         if (p->vt) cudaFree(p->vt);
         p->vt = nullptr;
@@ -235,18 +234,35 @@ static spmv_status run_segdot_global(spmv_plan_s *p, int kb, const void *const *
         p->vt_bytes = need;
     }
     CUDA_TRY(launch_interleave(p->vec_t == SPMV_F64, kbt, kb, in, len, p->vt, s));
+    return SPMV_OK;
+}
+
+// Several vectors of a segmented pass in one streaming of the nonzeros, read from the
+// interleaved copy vt through L2: FP64 with MODE_SEGDOT (2..KB_MAX vectors), the other value
+// types with MODE_VSEG (2..VL_MAX vectors, one per lane of a lane group).  Either way every
+// vector's sums are formed exactly as in its single-vector pass.
+static spmv_status run_segdot_global(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
+                                     spmv_plan_s *prof, int id_dot, int id_fix, int64_t in_len) {
+    const bool vseg = p->val_t != SPMV_F64;
+    const int mode = vseg ? MODE_VSEG : MODE_SEGDOT;
+    const int kbt = vseg ? (kb <= 4 ? 4 : 8) : kb_template(kb);
+    // VSEG stages the interleaved vectors (or each block's window of them) when they leave room
+    // for half of its warps
+    const bool smemv = vseg && warps_for(p, MODE_VSEG, kbt, true) >= std::min(p->W, WARPS_VSEG) / 2;
+    spmv_status st = interleave_inputs(p, kbt, kb, in, in_len >= 0 ? in_len : p->n_minor, s);
+    if (st != SPMV_OK) return st;
     LaunchArgs a;
     a.sp = base_params(p);
     a.sp.kb = kb;
     a.sp.vin[0] = p->vt;
     for (int b = 0; b < kb; ++b) a.sp.vout[b] = out[b];
-    set_geometry(p, a, MODE_SEGDOT, kbt, false);
+    set_geometry(p, a, mode, kbt, smemv);
     const spmv_plan_s::ProcZones &pz = p->pz;
     a.sp.nproc = pz.nproc;
     a.stream = s;
     {
         ProfScope ps(prof, id_dot, s);
-        CUDA_TRY(launch_stream(p, MODE_SEGDOT, kb, a));
+        CUDA_TRY(launch_stream(p, mode, kb, a));
     }
     if (pz.z > 0) {
         ProfScope ps(prof, id_fix, s);
@@ -255,10 +271,13 @@ static spmv_status run_segdot_global(spmv_plan_s *p, int kb, const void *const *
     return SPMV_OK;
 }
 
+// Vectors per pass of a plan's multi-vector segmented passes.
+static int seg_group(const spmv_plan_s *p) { return p->val_t == SPMV_F64 ? KB_MAX : VL_MAX; }
+
 // The segmented pass (and its zone fix-up) of plan p; the launches are timed as kernels
-// id_dot / id_fix of plan `prof`.  Up to batch_width vectors run with the short vector on chip;
-// more run (up to KB_MAX per pass) with the vectors interleaved in a plan-owned global buffer
-// (in_len entries each: the short vector, or the long vector of a row-sorted copy's windows).
+// id_dot / id_fix of plan `prof`.  One vector runs with the short vector on chip when it fits;
+// several run through run_segdot_global (FP64: on chip instead while batch_width holds them),
+// seg_group(p) per pass.
 static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s,
                                    spmv_plan_s *prof, int id_dot, int id_fix, int64_t in_len) {
     const size_t out_bytes = (size_t)p->n_major * p->sx;
@@ -267,9 +286,11 @@ static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in
             for (int b = 0; b < kb; ++b) CUDA_TRY(cudaMemsetAsync(out[b], 0, out_bytes, s));
         return SPMV_OK;
     }
-    if (kb > KB_MAX || (kb > 1 && (!p->onchip || kb > p->batch_width))) {
-        for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
-            const int kg = std::min(KB_MAX, kb - g0);
+    const bool f64_onchip = p->val_t == SPMV_F64 && p->onchip && kb <= p->batch_width;
+    if (kb > 1 && !f64_onchip) {
+        const int grp = seg_group(p);
+        for (int g0 = 0; g0 < kb; g0 += grp) {
+            const int kg = std::min(grp, kb - g0);
             spmv_status st = kg == 1 ? run_segdot_impl(p, 1, in + g0, out + g0, s, prof, id_dot, id_fix, in_len)
                                      : run_segdot_global(p, kg, in + g0, out + g0, s, prof, id_dot, id_fix, in_len);
             if (st != SPMV_OK) return st;
@@ -299,8 +320,9 @@ static spmv_status run_segdot_impl(spmv_plan_s *p, int kb, const void *const *in
 }
 
 spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
-    for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
-        const int kg = std::min(KB_MAX, kb - g0);
+    const int grp = seg_group(p);
+    for (int g0 = 0; g0 < kb; g0 += grp) {
+        const int kg = std::min(grp, kb - g0);
         spmv_status st = run_segdot_impl(p, kg, in + g0, out + g0, s, p, 2, 3, -1);
         if (st != SPMV_OK) return st;
     }
@@ -310,19 +332,20 @@ spmv_status run_segdot(spmv_plan_s *p, int kb, const void *const *in, void *cons
 // The short-vector product over the row-sorted blocks (SPMV_PLAN_ROW_BLOCKS): the sub-plan's
 // windowed segmented pass writes every block's short vector into ypart (its fix-up completes
 // the entries split between chunks), then the blocks' vectors are added in FP64 in block
-// order (Sec. III step 2).  One vector runs with its windows on chip; up to KB_MAX together read
-// their windows through L2 from an interleaved copy of the long vectors, into per-block vectors
-// [vector][block][n_minor] (a plan-owned buffer made on first use).
+// order (Sec. III step 2).  One vector runs with its windows on chip; several (seg_group per
+// pass) read their windows through L2 from an interleaved copy of the long vectors, into
+// per-block vectors [vector][block][n_minor] (a plan-owned buffer made on first use).
 static spmv_status run_row_blocks(spmv_plan_s *p, int kb, const void *const *in, void *const *out, cudaStream_t s) {
     spmv_plan_s *q = p->tplan;
     const bool f64 = p->vec_t == SPMV_F64;
     const size_t nseg = (size_t)p->blocks * p->n_minor;
-    for (int g0 = 0; g0 < kb; g0 += KB_MAX) {
-        const int kg = std::min(KB_MAX, kb - g0);
-        void *yp[KB_MAX];
+    const int grp = seg_group(q);
+    for (int g0 = 0; g0 < kb; g0 += grp) {
+        const int kg = std::min(grp, kb - g0);
+        void *yp[VL_MAX];
         void *base = p->ypart;
         if (kg > 1) {
-            const size_t need = nseg * KB_MAX * p->sx;
+            const size_t need = nseg * grp * p->sx;
             if (p->ypart_k_bytes < need) {
                 if (p->ypart_k) cudaFree(p->ypart_k);
                 p->ypart_k = nullptr;
@@ -651,7 +674,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     const size_t part_bytes = (pi && pi->segdot_only) ? 16
                               : p->onchip ? (size_t)p->ctas * p->batch_width * p->n_minor * p->sa
                                           : (size_t)p->n_minor * sizeof(double);
-    const size_t rec_bytes = (size_t)KB_MAX * p->max_nproc * 2 * p->sa;  // any segmented pass: up to KB_MAX vectors
+    const size_t rec_bytes = (size_t)VL_MAX * p->max_nproc * 2 * p->sa;  // any segmented pass: up to VL_MAX vectors
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);

@@ -15,11 +15,14 @@ enum Mode : int {
     MODE_SCATTER = 0,  // acc[idx[k]] += val[k] * w[major(k)]   (CSC A x, CSR v^T A)
     MODE_SEGDOT = 1,   // out[j] = sum_{k in segment j} val[k] * w[idx[k]]   (CSC v^T A, CSR A x)
     MODE_DVALUES = 2,  // g[k] = minor[idx[k]] * major[seg(k)]
+    MODE_VSEG = 3,     // MODE_SEGDOT for several vectors, one per lane of a lane group
 };
 
-constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels
+constexpr int KB_MAX = 8;        // vectors per pass of the multi-vector kernels (but MODE_VSEG)
+constexpr int VL_MAX = 8;        // vectors per pass of MODE_VSEG (lane group width)
 constexpr int MAX_WARPS = 24;    // warps per CTA of the single-vector passes (80 registers a thread beyond 16)
 constexpr int MAX_WARPS_KB = 16; // warps per CTA of the multi-vector passes
+constexpr int WARPS_VSEG = 16;   // warps per CTA of MODE_VSEG (up to 128 registers a thread)
 constexpr int WARPS_REGS = 16;   // warps per CTA up to which a kernel may use 128 registers a thread
 constexpr int MAX_STAGES = 4;    // slots per warp
 constexpr int BAR_BYTES = 1024;  // slot barriers at the start of the staging area
@@ -64,8 +67,9 @@ struct StreamParams {
     int32_t tile_cap, off_val, off_mask, off_x, off_hdr;  // slot layout: indices at 0, values, masks, windows, header
     int32_t checked;         // 1: indices not validated by the plan, checked (clamped) on every step
     int32_t kb;              // vectors in this pass (<= KB template)
-    const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major
-    void *vout[KB_MAX];      // SEGDOT: major outputs; DVALUES: vout[0] = g
+    const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major;
+                             // VSEG: vin[0] = the minor vectors interleaved [entry][VL]
+    void *vout[VL_MAX];      // SEGDOT, VSEG: major outputs; DVALUES: vout[0] = g
     void *part;              // SCATTER: per-CTA partials [cta][kb][n_minor] (on chip) or FP64 accumulator [kb][n_minor]
     void *rec_left, *rec_right;  // SEGDOT carry records [b * nproc + proc]: (hi, lo) pairs of the accumulation type
     int32_t nproc;           // processors (chunks of tiles) of the plan: the record stride
@@ -120,7 +124,7 @@ cudaError_t launch_stream_f16(int mode, int kb, const LaunchArgs &a);
 cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int nparts, int n_minor, int kb,
                            void *const *out, cudaStream_t s, size_t qstride = 0, size_t bstride = 0);
 // out[i * kbt + b] = in[b][i] (zeros for kb <= b < kbt), i < len: vectors interleaved for the
-// multi-vector segmented pass over global memory (kbt = 2, 4 or 8).
+// multi-vector segmented passes (kbt = 2, 4 or 8).
 cudaError_t launch_interleave(bool f64, int kbt, int kb, const void *const *in, int64_t len, void *out,
                               cudaStream_t s);
 cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,

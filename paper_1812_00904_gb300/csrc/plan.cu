@@ -459,11 +459,16 @@ int stream_processors(int ntiles, int T, int nnz, int ctas, int C, int32_t *nzb)
 // Plan-owned copy of the nonzeros, permuted within every major segment (a column of a
 // CSC matrix, a row of a CSR one), so that the minor indices one warp instruction of the
 // streaming kernels reads or updates in shared memory fall into distinct banks.  The
-// streaming kernels touch tile positions r (r = nonzero position mod T) in two patterns:
-// the scatter pass 32 consecutive ones (r = 32a + b, b = 0..31), the segmented pass one of
-// 8 positions per lane, 8l + (e ^ 4((l >> 2) & 1)).  A position r asks for bank
-// ((r & 31) + ((r >> 5) & 7)) mod NB, which is one-to-one over the lanes in both patterns
-// (NB = 32 banks of 4-byte words; 16 for 8-byte elements).  One thread per segment: its
+// streaming kernels touch tile positions r (r = nonzero position mod T) in these patterns:
+// the scatter pass 32 consecutive ones (r = 32a + b, b = 0..31); the segmented pass one of
+// 8 positions per lane, 8l + (e ^ 4((l >> 2) & 1)); the multi-vector segmented pass, whose
+// lane groups read the VL consecutive words of one index each (VL = 8: 4 groups at positions
+// 32a + 8c + e, c = 0..3, so that the index mod 4 picks the group's banks; VL = 4: 8 groups
+// at 64a + 8c + e, c = 0..7, index mod 8).  With 4-byte words (32 banks) position
+// r = 256 t + 32a + 8c + e asks for bank (4a + c + 4e) mod 32, one-to-one over the lanes
+// of the first two patterns and over the groups of the third; with 8-byte words (16 banks)
+// for ((r & 31) + ((r >> 5) & 7)) mod 16, one-to-one over each half of the lanes of the
+// first two.  One thread per segment: its
 // nonzeros are pooled by bank; every position, in order, takes a nonzero of the bank it
 // asks for while that pool lasts, else one of the fullest pool.  Within a bank the stored
 // order is kept.  Each thread reads and writes only its clamped range [s, e), so a
@@ -501,7 +506,7 @@ __global__ void bank_order_kernel(const int32_t *__restrict__ ptr, int n_major, 
     // slots[s + off[b] ..]
     int r = s % T;
     for (int q = s; q < e; ++q) {
-        int b = ((r & 31) + ((r >> 5) & 7)) & nbm;
+        int b = nbm == 31 ? (4 * ((r >> 5) & 7) + ((r >> 3) & 3) + 4 * (r & 7)) & 31 : ((r & 31) + ((r >> 5) & 7)) & nbm;
         if (used[b] == cnt[b]) {
             int left = -1;
             for (int k = 0; k <= nbm; ++k) {

@@ -75,9 +75,9 @@ struct spmv_plan_s {
     void *bown = nullptr;       // the sorted copy's indices and values (when the sub-plan borrows them)
     size_t bown_bytes = 0;
     void *ypart = nullptr;      // per-block short vectors [block][n_minor]
-    void *ypart_k = nullptr;    // the same for up to KB_MAX vectors, [vector][block][n_minor] (made on first use)
+    void *ypart_k = nullptr;    // the same for several vectors, [vector][block][n_minor] (made on first use)
     size_t ypart_k_bytes = 0;
-    void *vt = nullptr;         // up to KB_MAX input vectors interleaved, for multi-vector segmented passes
+    void *vt = nullptr;         // up to VL_MAX input vectors interleaved, for multi-vector segmented passes
     size_t vt_bytes = 0;        // over vectors that stay in global memory (made on first use)
     const int2 *win = nullptr;  // sub-plan: per CTA window of the long vector
 

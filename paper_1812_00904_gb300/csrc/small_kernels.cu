@@ -13,10 +13,10 @@
 namespace gbk {
 
 struct OutPtrs {
-    void *p[KB_MAX];
+    void *p[VL_MAX];
 };
 struct InPtrs {
-    const void *p[KB_MAX];
+    const void *p[VL_MAX];
 };
 
 // An FP32 value widened to FP64 exactly.  Normal numbers by moving the sign, exponent
@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(256) fixup_kernel(const ZoneDev *__restrict__ 
 cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int nparts, int n_minor, int kb,
                            void *const *out, cudaStream_t s, size_t qstride, size_t bstride) {
     if (n_minor <= 0) return cudaSuccess;
+    if (kb < 1 || kb > VL_MAX) return cudaErrorInvalidValue;
     OutPtrs o;
-    for (int b = 0; b < KB_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
+    for (int b = 0; b < VL_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
     if (qstride == 0) {  // [part][vector][element]
         qstride = (size_t)kb * n_minor;
         bstride = (size_t)n_minor;
@@ -125,25 +126,35 @@ cudaError_t launch_combine(bool vec_f64, bool part_f64, const void *part, int np
 }
 
 // out[i * KB + b] = in_b[i] for b < kb, 0 for kb <= b < KB: k vectors interleaved for the
-// multi-vector segmented pass over vectors kept in global memory.
+// multi-vector segmented passes over vectors kept in global memory.  A block moves IT
+// consecutive entries of every vector: coalesced reads of each vector into shared memory,
+// then coalesced writes of the interleaved rows.
 template <typename XT, int KB>
-__global__ void interleave_kernel(InPtrs in, int kb, int64_t len, XT *__restrict__ out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
-        XT v[KB];
+__global__ void __launch_bounds__(256) interleave_kernel(InPtrs in, int kb, int64_t len, XT *__restrict__ out) {
+    constexpr int IT = 256;
+    constexpr int RS = KB + 1;  // padded row: no bank conflicts in either phase
+    __shared__ XT sh[IT * RS];
+    for (int64_t i0 = (int64_t)blockIdx.x * IT; i0 < len; i0 += (int64_t)gridDim.x * IT) {
+        const int cnt = (int)(len - i0 < IT ? len - i0 : (int64_t)IT);
 #pragma unroll
-        for (int b = 0; b < KB; ++b) v[b] = b < kb ? static_cast<const XT *>(in.p[b])[i] : XT(0);
-#pragma unroll
-        for (int b = 0; b < KB; ++b) out[i * KB + b] = v[b];
+        for (int b = 0; b < KB; ++b) {
+            const XT *src = b < kb ? static_cast<const XT *>(in.p[b]) : nullptr;
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) sh[t * RS + b] = src ? src[i0 + t] : XT(0);
+        }
+        __syncthreads();
+        XT *dst = out + i0 * KB;
+        for (int t = threadIdx.x; t < cnt * KB; t += blockDim.x) dst[t] = sh[(t / KB) * RS + t % KB];
+        __syncthreads();
     }
 }
 
 cudaError_t launch_interleave(bool f64, int kbt, int kb, const void *const *in, int64_t len, void *out,
                               cudaStream_t s) {
     if (len <= 0) return cudaSuccess;
+    if (kb < 1 || kb > kbt || kbt > VL_MAX || (f64 && kbt > KB_MAX)) return cudaErrorInvalidValue;
     InPtrs ip;
-    for (int b = 0; b < KB_MAX; ++b) ip.p[b] = b < kb ? in[b] : nullptr;
-    const int grid = (int)std::min<int64_t>((len + 255) / 256, 152 * 16);
+    for (int b = 0; b < VL_MAX; ++b) ip.p[b] = b < kb ? in[b] : nullptr;
+    const int grid = (int)std::min<int64_t>((len + 255) / 256, 152 * 8);
     if (f64) {
         double *o = static_cast<double *>(out);
         if (kbt == 2) interleave_kernel<double, 2><<<grid, 256, 0, s>>>(ip, kb, len, o);
@@ -161,8 +172,9 @@ cudaError_t launch_interleave(bool f64, int kbt, int kb, const void *const *in, 
 cudaError_t launch_fixup(bool vec_f64, const ZoneDev *zones, int z, const void *rec_left, const void *rec_right,
                          int P, int kb, void *const *out, cudaStream_t s) {
     if (z <= 0) return cudaSuccess;
+    if (kb < 1 || kb > VL_MAX) return cudaErrorInvalidValue;
     OutPtrs o;
-    for (int b = 0; b < KB_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
+    for (int b = 0; b < VL_MAX; ++b) o.p[b] = b < kb ? out[b] : nullptr;
     const int grid = (z + 255) / 256;
     if (vec_f64)
         fixup_kernel<double, double2><<<grid, 256, 0, s>>>(zones, z, static_cast<const double2 *>(rec_left),

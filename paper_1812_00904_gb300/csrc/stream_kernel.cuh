@@ -30,6 +30,10 @@
 //                 that continue in the neighbouring chunks (overlap zones) leave
 //                 their partial sums in the chunk's carry records for the zone
 //                 fixup.
+//   MODE_VSEG:    MODE_SEGDOT for several vectors in one pass: a lane group of VL lanes
+//                 holds one vector per lane, and each lane forms its vector's sums with
+//                 the same operations in the same order as the single-vector pass, so
+//                 every vector's result equals its single-vector product bit for bit.
 //   MODE_DVALUES: g[k] = minor[idx[k]] * major[seg(k)].
 #pragma once
 
@@ -51,6 +55,11 @@ __device__ __forceinline__ void copy_elem(unsigned char *d, const unsigned char 
 }
 
 template <typename XT> __device__ __forceinline__ XT zero_of() { return XT(0); }
+
+// A product rounded on its own (never fused into a following addition), so that the
+// segmented passes round every product the same way whatever code surrounds it.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // carry records: (hi, lo) of the accumulation type, widened to FP64 by the zone fixup
 template <typename T> struct Pair;
@@ -90,6 +99,7 @@ struct RtBool {  // a flag known only at run time, passed where a BoolC may be
 template <typename VT, typename XT, int MODE, int KB, bool SMEMV, int WB>
 __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constant__ StreamParams p) {
     using AT = typename Acc<VT>::type;
+    constexpr bool SEGM = MODE == MODE_SEGDOT || MODE == MODE_VSEG;  // a segmented (dot-product) pass
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -174,7 +184,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     auto xwindow = [&](int i0, int i1, int &xbase, int &nxc) {
         xbase = 0;
         nxc = 0;
-        if constexpr (MODE != MODE_SEGDOT) {
+        if constexpr (!SEGM) {
             constexpr int xa = 16 / (int)sizeof(XT);
             const int last = min(i1, p.n_major - 1);
             if (last >= i0) {
@@ -203,7 +213,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         c_off = p.off_x + b * p.x_cap * (int)sizeof(XT);
         c_len = p.n_major;
         c_es = (int)sizeof(XT);
-        c_x = MODE != MODE_SEGDOT && b < nvec;
+        c_x = !SEGM && b < nvec;
     }
     const int c_lim = c_len & ~(16 / c_es - 1);  // the array's last 16-byte boundary (in elements)
     // issue the copies of tile k into slot s
@@ -253,32 +263,38 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     // sbar, whose phases sphase counts.
     uint64_t *sbar = reinterpret_cast<uint64_t *>(smem + p.vec_region_bytes + BAR_BYTES) - 1;
     uint32_t sphase = 0;
-    if (SMEMV && MODE != MODE_SCATTER && KB == 1 && threadIdx.x == 0) {
+    // VSEG: the short vectors interleaved ([entry][VL], a whole entry VL * 4 bytes) follow the
+    // lanes' scratch at the start of the region
+    constexpr int VSCR_BYTES = WARPS_VSEG * 32 * 8 * 4;
+    constexpr bool BULKV = SMEMV && (MODE == MODE_VSEG || (MODE != MODE_SCATTER && KB == 1));
+    if (BULKV && threadIdx.x == 0) {
         mbar_init(sbar, 1);
         fence_mbar_init();
     }
     auto stage_vector = [&](int gbk) {
         if constexpr (SMEMV && MODE != MODE_SCATTER) {
-            XT *vs = reinterpret_cast<XT *>(smem);
+            constexpr int EW = MODE == MODE_VSEG ? KB : 1;  // values per entry of the staged vector
+            XT *vs = reinterpret_cast<XT *>(smem + (MODE == MODE_VSEG ? VSCR_BYTES : 0));
             int wb = 0, wl = p.n_minor;
-            if (MODE == MODE_SEGDOT && p.win) {
+            if (p.win) {
                 const int2 w = p.win[gbk];
                 wb = w.x;
                 wl = min(w.y, p.n_minor);
             }
-            if constexpr (KB == 1) {
+            if constexpr (BULKV) {
                 // its 16-byte aligned part by bulk copies, the rest (under 16 bytes) by plain loads
-                const XT *src = static_cast<const XT *>(p.vin[0]) + wb;
-                constexpr int xa = 16 / (int)sizeof(XT);
+                const XT *src = static_cast<const XT *>(p.vin[0]) + (size_t)wb * EW;
+                constexpr int xa = (16 / (int)sizeof(XT) + EW - 1) / EW;  // entries per 16 bytes (at least 1)
                 const int wbulk = wl & ~(xa - 1);
                 if (threadIdx.x == 0 && wbulk > 0) {
-                    mbar_arrive_expect_tx(sbar, static_cast<uint32_t>(wbulk) * (uint32_t)sizeof(XT));
+                    mbar_arrive_expect_tx(sbar, static_cast<uint32_t>(wbulk) * EW * (uint32_t)sizeof(XT));
                     constexpr int piece = 32768 / (int)sizeof(XT);
-                    for (int o = 0; o < wbulk; o += piece)
-                        bulk_g2s(vs + o, src + o, static_cast<uint32_t>(min(piece, wbulk - o)) * (uint32_t)sizeof(XT),
+                    const int total = wbulk * EW;
+                    for (int o = 0; o < total; o += piece)
+                        bulk_g2s(vs + o, src + o, static_cast<uint32_t>(min(piece, total - o)) * (uint32_t)sizeof(XT),
                                  sbar);
                 }
-                for (int i = wbulk + threadIdx.x; i < wl; i += blockDim.x) vs[i] = src[i];
+                for (int i = wbulk * EW + threadIdx.x; i < wl * EW; i += blockDim.x) vs[i] = src[i];
                 __syncthreads();  // the barrier's initialisation before anyone waits on it
                 if (wbulk > 0) {
                     if (!mbar_wait_bounded(sbar, sphase & 1u, WAIT_LIMIT_NS)) {
@@ -328,7 +344,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
     __syncthreads();
     cfirst = -1;
     cleft = false;
-    vwin = (MODE == MODE_SEGDOT && p.win) ? p.win[gb].x : 0;
+    vwin = (SEGM && p.win) ? p.win[gb].x : 0;
 #pragma unroll
     for (int b = 0; b < KB; ++b) {
         chi[b] = AT(0);
@@ -406,7 +422,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     }
                     return lo;
                 };
-                if constexpr (MODE == MODE_SEGDOT) {
+                if constexpr (SEGM) {
                     if (dup) {  // empty segments ending in this tile get zero
                         for (int j = i0 + 1 + lane; j < i1; j += 32)
                             if (p.pptr[j + 1] == p.pptr[j]) {
@@ -678,7 +694,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             }
 #pragma unroll
                             for (int b = 0; b < KB; ++b) {
-                                const AT pe = vae * static_cast<AT>(wv[b]);
+                                const AT pe = mul_rn(vae, static_cast<AT>(wv[b]));
                                 rr[e][b] = (e == 0 || ((hb >> e) & 1u)) ? pe : rr[e > 0 ? e - 1 : 0][b] + pe;
                             }
                         }
@@ -697,7 +713,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                     w_ = static_cast<AT>(__ldg(static_cast<const XT *>(p.vin[b]) + vwin + ix[e]));
                                 }
                             }
-                            pr[e] = va[e] * w_;
+                            pr[e] = mul_rn(va[e], w_);
                         }
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
@@ -794,16 +810,276 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     }
                 };
 
-                if constexpr (MODE == MODE_SEGDOT) {
-                    if (full && !dup && !p.checked)
-                        run_segdot8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
-                    else
-                        run_segdot8(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
+
+                // ---- VSEG: several vectors, one per lane of a lane group.  Lane g VL + bv carries
+                // vector bv through the virtual lanes v = g + NG i (i < VL) of every 256-position
+                // step, virtual lane v being the 8 positions 8v .. 8v + 7 that lane v takes in the
+                // single-vector pass.  Each sum is formed with that pass's operations in its order:
+                // the prefix of a virtual lane restarted at every head, the butterfly total of a
+                // head-free step, the segmented Kogge-Stone scan over the 32 virtual lanes of a step
+                // with heads (levels within a lane on registers, the others by shuffles across the
+                // lane groups) and the compensated carry.  The vectors are read through L2 from an
+                // interleaved copy, vin[0][i * VL + b].
+                auto run_vseg = [&](auto fast_tag, auto full_tag, auto check_tag) {
+                    constexpr int VL = KB;
+                    constexpr int NG = 32 / VL;
+                    static_assert(MODE != MODE_VSEG || (VL >= 4 && VL <= VL_MAX && 32 % VL == 0), "lane groups of 4 or 8");
+                    constexpr bool WHOLE = decltype(full_tag)::value;
+                    constexpr bool CHECK = decltype(check_tag)::value;
+                    const bool FAST = fast_tag.value;  // compile-time (BoolC) or run-time (RtBool)
+                    const int g = lane / VL;
+                    const int bv = lane - g * VL;
+                    const bool act = bv < kb;
+                    const float *vt = static_cast<const float *>(p.vin[0]) + bv;  // in global memory
+                    const float *vsm = reinterpret_cast<const float *>(smem + VSCR_BYTES) + bv;  // staged (SMEMV)
+                    // this lane's 8-value scratch (the region before the staging slots)
+                    AT *vscr = reinterpret_cast<AT *>(smem) + (warp * 32 + lane) * 8;
+                    const int nsteps = (rel_hi + 255) >> 8;
+                    for (int stp = 0; stp < nsteps; ++stp) {
+                        // the step's segment-start words (positions 256 stp + 32 j ..), and its
+                        // virtual lanes that hold a head (bit v)
+                        uint32_t w[8];
+                        {
+                            const uint4 qa = reinterpret_cast<const uint4 *>(mask_s)[2 * stp];
+                            const uint4 qb = reinterpret_cast<const uint4 *>(mask_s)[2 * stp + 1];
+                            w[0] = qa.x; w[1] = qa.y; w[2] = qa.z; w[3] = qa.w;
+                            w[4] = qb.x; w[5] = qb.y; w[6] = qb.z; w[7] = qb.w;
+                            if (!WHOLE) {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e)
+                                    if ((stp << 3) + e >= p.mwp) w[e] = 0u;
+                            }
+                        }
+                        unsigned bal;
+                        {
+                            const int wi = (stp << 3) + (lane >> 2);
+                            const uint32_t wl = (WHOLE || wi < p.mwp) ? mask_s[wi] : 0u;
+                            bal = __ballot_sync(FULL, ((wl >> ((lane & 3) << 3)) & 0xFFu) != 0u);
+                        }
+                        // word of the step holding virtual lane i's bits (NG = 8: one of two)
+                        auto word_of = [&](int i) -> uint32_t {
+                            constexpr int NW = NG > 4 ? 2 : 1;
+                            const int wlo = (NG * i) >> 2;
+                            uint32_t wv = w[wlo];
+                            if constexpr (NW > 1) {
+                                if (((g + NG * i) >> 2) != wlo) wv = w[wlo + 1];
+                            }
+                            return wv;
+                        };
+                        auto heads_of = [&](int i) -> uint32_t {
+                            return (word_of(i) >> (((g + NG * i) & 3) << 3)) & 0xFFu;
+                        };
+                        // heads of the tile before virtual lane i (the single-vector pass's base)
+                        const int cbs = __shfl_sync(FULL, cnt_ex, stp << 3);
+                        auto base_of = [&](int i) -> int {
+                            const int v = g + NG * i;
+                            int pre = 0;
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                if (j < (v >> 2)) pre += __popc(w[j]);
+                            return cbs + pre + __popc(word_of(i) & ((1u << ((v & 3) << 3)) - 1u));
+                        };
+                        // products of virtual lane i's 8 positions in position order (+0 outside the tile)
+                        auto products = [&](int i, AT (&pe)[8]) {
+                            const int p0 = (stp << 8) + ((g + NG * i) << 3);
+                            uint32_t vm = 0xFFu;
+                            if constexpr (!WHOLE) {
+                                const int lo_cut = min(max(rel_lo - p0, 0), 8);
+                                const int hi_cut = min(max(rel_hi - p0, 0), 8);
+                                vm = ((1u << hi_cut) - 1u) & ~((1u << lo_cut) - 1u);
+                            }
+                            int ix[8];
+                            AT va[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                ix[e] = 0;
+                                va[e] = AT(0);
+                            }
+                            if (WHOLE || vm) {
+                                const int4 qa = reinterpret_cast<const int4 *>(idx_s)[p0 >> 2];
+                                const int4 qb = reinterpret_cast<const int4 *>(idx_s)[(p0 >> 2) + 1];
+                                ix[0] = qa.x; ix[1] = qa.y; ix[2] = qa.z; ix[3] = qa.w;
+                                ix[4] = qb.x; ix[5] = qb.y; ix[6] = qb.z; ix[7] = qb.w;
+                                Load8<VT, AT>::run(val_s, p0, va);
+                                if (!WHOLE) {
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e)
+                                        if (!((vm >> e) & 1u)) {
+                                            ix[e] = 0;
+                                            va[e] = AT(0);
+                                        }
+                                }
+                                if constexpr (CHECK) {
+                                    unsigned mx = 0;
+#pragma unroll
+                                    for (int e = 0; e < 8; ++e) {
+                                        mx = max(mx, static_cast<unsigned>(ix[e]));
+                                        ix[e] = static_cast<int>(min(static_cast<unsigned>(ix[e]), n_minor - 1u));
+                                    }
+                                    idx_bad |= mx >= n_minor;
+                                }
+                            }
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                AT wv = AT(0);
+                                if (act && (WHOLE || ((vm >> e) & 1u))) {
+                                    if constexpr (SMEMV) {
+                                        wv = vsm[ix[e] * VL];
+                                    } else {
+                                        wv = __ldg(vt + (size_t)(vwin + ix[e]) * VL);
+                                    }
+                                }
+                                pe[e] = mul_rn(va[e], wv);
+                            }
+                        };
+                        if (bal == 0u) {
+                            // head-free step: the butterfly total (xor 16, 8, .., 1 over the virtual
+                            // lanes: the levels within a lane first, then across the lane groups)
+                            AT t[VL];
+#pragma unroll
+                            for (int i = 0; i < VL; ++i) {
+                                AT pe[8];
+                                products(i, pe);
+                                AT r = pe[0];
+#pragma unroll
+                                for (int e = 1; e < 8; ++e) r = r + pe[e];
+                                t[i] = r;
+                            }
+#pragma unroll
+                            for (int h = VL / 2; h >= 1; h >>= 1) {
+#pragma unroll
+                                for (int i = 0; i < h; ++i) t[i] = t[i] + t[i + h];
+                            }
+                            AT tot = t[0];
+#pragma unroll
+                            for (int d = NG / 2; d >= 1; d >>= 1) tot = tot + __shfl_xor_sync(FULL, tot, d * VL);
+                            const AT s_ = chi[0] + tot;
+                            const AT bp = s_ - chi[0];
+                            clo[0] += (chi[0] - (s_ - bp)) + (tot - bp);
+                            chi[0] = s_;
+                            continue;
+                        }
+                        // step with heads: every virtual lane's open sum at its end (T), the open sum
+                        // before its first head (F); segments closing at its later heads are emitted
+                        // here, from the lane's scratch of the values that close at each position
+                        AT T[VL], F[VL];
+#pragma unroll
+                        for (int i = 0; i < VL; ++i) {
+                            const uint32_t hb = heads_of(i);
+                            AT pe[8];
+                            products(i, pe);
+                            AT rr[8];
+                            rr[0] = pe[0];
+#pragma unroll
+                            for (int e = 1; e < 8; ++e) rr[e] = ((hb >> e) & 1u) ? pe[e] : rr[e - 1] + pe[e];
+                            T[i] = rr[7];
+                            F[i] = AT(0);
+                            if (hb) {
+                                // value closing at position e: the open sum up to e - 1 (0 at e = 0)
+                                float4 *q = reinterpret_cast<float4 *>(vscr);
+                                q[0] = make_float4(0.f, rr[0], rr[1], rr[2]);
+                                q[1] = make_float4(rr[3], rr[4], rr[5], rr[6]);
+                                F[i] = vscr[__ffs(hb) - 1];
+                                uint32_t rem = hb & (hb - 1u);
+                                if (act && rem) {
+                                    const int p0 = (stp << 8) + ((g + NG * i) << 3);
+                                    XT *o = static_cast<XT *>(p.vout[bv]);
+                                    int col = FAST ? i0 + base_of(i) : 0;
+                                    while (rem) {  // a later head: the segment lies inside the virtual lane
+                                        const int e = __ffs(rem) - 1;
+                                        col = FAST ? col + 1 : col_search(p0 + e - 1);
+                                        o[col] = static_cast<XT>(vscr[e]);
+                                        rem &= rem - 1u;
+                                    }
+                                }
+                            }
+                        }
+                        // segmented Kogge-Stone scan of the open sums over the 32 virtual lanes: at
+                        // level d virtual lane v adds the sum of v - d when no head lies in
+                        // (v - d, v] and v >= d (bit v of ok)
+                        unsigned ok = ~bal & ~1u;
+#pragma unroll
+                        for (int lv = 0; lv < 5; ++lv) {
+                            const int d = 1 << lv;
+                            if (lv > 0) ok &= ok << (d >> 1);
+                            if (d < NG) {
+                                // from lane group (g - d) mod NG: its sum of the same i, or of i - 1
+                                // when the distance wraps past group NG - 1
+                                const bool wsrc = g + d >= NG;
+                                const int src = ((g + NG - d) % NG) * VL + bv;
+                                AT rv[VL];
+#pragma unroll
+                                for (int i = 0; i < VL; ++i)
+                                    rv[i] = __shfl_sync(FULL, wsrc ? (i > 0 ? T[i > 0 ? i - 1 : 0] : AT(0)) : T[i], src);
+#pragma unroll
+                                for (int i = 0; i < VL; ++i)
+                                    if ((ok >> (g + NG * i)) & 1u) T[i] = T[i] + rv[i];
+                            } else {
+                                const int dd = d / NG;
+#pragma unroll
+                                for (int i = VL - 1; i >= dd; --i)
+                                    if ((ok >> (g + NG * i)) & 1u) T[i] = T[i] + T[i - dd];
+                            }
+                        }
+                        // open sum at the end of virtual lane v - 1 (0 for v = 0)
+                        AT Tex[VL];
+                        {
+                            const bool wsrc = g == NG - 1;
+                            const int src = ((g + NG - 1) % NG) * VL + bv;
+#pragma unroll
+                            for (int i = 0; i < VL; ++i) {
+                                if constexpr (NG > 1) {
+                                    Tex[i] = __shfl_sync(FULL, wsrc ? (i > 0 ? T[i > 0 ? i - 1 : 0] : AT(0)) : T[i], src);
+                                } else {
+                                    Tex[i] = i > 0 ? T[i > 0 ? i - 1 : 0] : AT(0);
+                                }
+                            }
+                            if (g == 0) Tex[0] = AT(0);
+                        }
+                        // the first head of each virtual lane closes the segment flowing into it
+                        const AT cc = chi[0] + clo[0];
+#pragma unroll
+                        for (int i = 0; i < VL; ++i) {
+                            const uint32_t hb = heads_of(i);
+                            if (act && hb) {
+                                const int v = g + NG * i;
+                                const bool before = (bal & ((1u << v) - 1u)) != 0u;
+                                const AT lead = Tex[i] + (before ? AT(0) : cc);
+                                const AT val = F[i] + lead;
+                                const int e = __ffs(hb) - 1;
+                                emit(FAST ? i0 + base_of(i) : col_search((stp << 8) + (v << 3) + e - 1), bv, val);
+                            }
+                        }
+                        chi[0] = __shfl_sync(FULL, T[VL - 1], (NG - 1) * VL + bv);
+                        clo[0] = AT(0);
+                    }
+                };
+
+                if constexpr (SEGM) {
+                    if constexpr (MODE == MODE_SEGDOT) {
+                        if (full && !dup && !p.checked)
+                            run_segdot8(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                        else
+                            run_segdot8(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
+                    } else {
+                        if (full && !dup && !p.checked)
+                            run_vseg(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                        else
+                            run_vseg(RtBool{!dup}, BoolC<false>{}, BoolC<true>{});
+                    }
                     // a segment whose end event lies in this tile is complete; the open one
                     // continues in the chunk's next tile (kept in chi, clo) or, at the end of
                     // the chunk, in the next chunk: right carry record
                     const int col_last = dup ? col_search(rel_hi - 1) : i0 + htotal;
-                    if (lane == 0) {
+                    if constexpr (MODE == MODE_VSEG) {
+                        if (lane < kb) {  // lane group 0 holds every vector's carry (lane = vector)
+                            const AT v = chi[0] + clo[0];
+                            if (col_last < i1)
+                                emit(col_last, lane, v);
+                            else if (needRight)
+                                static_cast<AT2 *>(p.rec_right)[(size_t)lane * p.nproc + proc] = make_pair2(chi[0], clo[0]);
+                        }
+                    } else if (lane == 0) {
                         for (int b = 0; b < kb; ++b) {
                             const AT v = chi[b] + clo[b];
                             if (col_last < i1)
@@ -884,6 +1160,50 @@ cudaError_t launch_one(const LaunchArgs &a) {
         if (a.block > WARPS_REGS * 32) return launch_wb<VT, XT, MODE, KB, SMEMV, MAX_WARPS>(a);
     }
     return launch_wb<VT, XT, MODE, KB, SMEMV, WARPS_REGS>(a);
+}
+
+// The instantiation for a pass of `mode` over kb vectors (kb rounded up to the template's).
+// FP64 runs several vectors of a segmented pass with MODE_SEGDOT (on chip or interleaved in
+// global memory); the other value types with MODE_VSEG (lane groups of 4 or 8, the vectors
+// staged in shared memory when they fit, else read through L2).
+template <typename VT, typename XT>
+cudaError_t launch_mode(int mode, int kb, const LaunchArgs &a) {
+    constexpr bool F64 = sizeof(VT) == 8;
+    if (mode == MODE_DVALUES) {
+        return a.smemv ? launch_one<VT, XT, MODE_DVALUES, 1, true>(a) : launch_one<VT, XT, MODE_DVALUES, 1, false>(a);
+    }
+    if (mode == MODE_VSEG) {
+        if constexpr (F64) {
+            return cudaErrorInvalidValue;
+        } else {
+            if (kb < 1 || kb > 8) return cudaErrorInvalidValue;
+            if (a.smemv)
+                return kb <= 4 ? launch_wb<VT, XT, MODE_VSEG, 4, true, WARPS_VSEG>(a)
+                               : launch_wb<VT, XT, MODE_VSEG, 8, true, WARPS_VSEG>(a);
+            return kb <= 4 ? launch_wb<VT, XT, MODE_VSEG, 4, false, WARPS_VSEG>(a)
+                           : launch_wb<VT, XT, MODE_VSEG, 8, false, WARPS_VSEG>(a);
+        }
+    }
+    if (mode == MODE_SCATTER) {
+        if (!a.smemv) return kb == 1 ? launch_one<VT, XT, MODE_SCATTER, 1, false>(a) : cudaErrorInvalidValue;
+        if (kb <= 1) return launch_one<VT, XT, MODE_SCATTER, 1, true>(a);
+        if (kb <= 2) return launch_one<VT, XT, MODE_SCATTER, 2, true>(a);
+        if (kb <= 4) return launch_one<VT, XT, MODE_SCATTER, 4, true>(a);
+        return launch_one<VT, XT, MODE_SCATTER, 8, true>(a);
+    }
+    if (kb <= 1) return a.smemv ? launch_one<VT, XT, MODE_SEGDOT, 1, true>(a) : launch_one<VT, XT, MODE_SEGDOT, 1, false>(a);
+    if constexpr (!F64) {
+        return cudaErrorInvalidValue;  // several vectors: MODE_VSEG
+    } else {
+        if (!a.smemv) {  // interleaved in global memory (vin[0])
+            if (kb <= 2) return launch_one<VT, XT, MODE_SEGDOT, 2, false>(a);
+            if (kb <= 4) return launch_one<VT, XT, MODE_SEGDOT, 4, false>(a);
+            return launch_one<VT, XT, MODE_SEGDOT, 8, false>(a);
+        }
+        if (kb <= 2) return launch_one<VT, XT, MODE_SEGDOT, 2, true>(a);
+        if (kb <= 4) return launch_one<VT, XT, MODE_SEGDOT, 4, true>(a);
+        return launch_one<VT, XT, MODE_SEGDOT, 8, true>(a);
+    }
 }
 
 }  // namespace gbk
