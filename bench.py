@@ -374,17 +374,19 @@ def ops_alone(pkg, plan, m, n, nnz, reps: int = 15, per: int = 20):
     return out
 
 
-def batched_rate(pkg, plan, m, n, nnz, k, steps):
-    """Vectors/s and effective GB/s of k-vector SpMV and SpVTM passes (matrix streamed once per pass)."""
+def batched_rate(pkg, plan, m, n, nnz, k, steps, ops=("spmv", "spvtm")):
+    """Vectors/s and effective GB/s of k-vector SpMV and SpVTM calls (spmv_batch)."""
     import torch
 
     dev = plan.vals.device
     g = torch.Generator(device=dev)
     g.manual_seed(13)
-    X = torch.rand((k, n), generator=g, device=dev)
-    V = torch.rand((k, m), generator=g, device=dev)
+    X = torch.rand((k, n), generator=g, device=dev) if "spmv" in ops else None
+    V = torch.rand((k, m), generator=g, device=dev) if "spvtm" in ops else None
     out = {}
     for op, inp, len_out in ((pkg.SPMV_OP_AX, X, m), (pkg.SPMV_OP_VTA, V, n)):
+        if inp is None:
+            continue
         Y = torch.empty((k, len_out), device=dev)
         for _ in range(2):
             pkg.spmv_batch(plan.handle, op, k, inp, inp.stride(0), Y, Y.stride(0))
@@ -682,7 +684,26 @@ def run_ours(args):
             br = batched_rate(pkg, plan, m, n, nnz, kk, max(10, args.steps // (5 * kk)))
             for op in ("spmv", "spvtm"):
                 br[op]["vs_single_vector"] = round(br[op]["vectors_per_s"] / single[op], 2)
+            br["path"] = {"spvtm": "one pass per 8 vectors, a vector per lane of a lane group; the 8 short vectors "
+                                   f"({m} x 8 x 4 B) do not fit on chip and are read through L2",
+                          "spmv": "shared-memory atomic passes, one per vector (the accumulators of 8 vectors do "
+                                  "not fit on chip)" if not blocks else
+                                  "over the row-sorted copy, one pass per 8 vectors (windows through L2)"}
             extras[f"batched_k{kk}"] = br
+        # multi-vector passes where 8 short vectors fit on chip: the same recipe with m = 2,000 rows
+        Sm = synth.wide_fp32_short(2000, device=dev)
+        ps = pkg.Plan(Sm.m, Sm.n, Sm.ptr, Sm.idx, Sm.vals, layout="csc", flags=order)
+        so = ops_alone(pkg, ps, Sm.m, Sm.n, Sm.nnz)
+        small_single = {"spmv": 1e3 / so["spmv"]["ms_median"], "spvtm": 1e3 / so["spvtm"]["ms_median"]}
+        extras["batched_short_m"] = {"workload": f"wide_csc_m{Sm.m}_n{Sm.n}_fp32_powerlaw2_50dense", "nnz": Sm.nnz,
+                                     "single_ms": {"spmv": so["spmv"]["ms_median"], "spvtm": so["spvtm"]["ms_median"]}}
+        for kk in (4, 8):
+            br = batched_rate(pkg, ps, Sm.m, Sm.n, Sm.nnz, kk, max(10, args.steps // (5 * kk)))
+            for op in ("spmv", "spvtm"):
+                br[op]["vs_single_vector"] = round(br[op]["vectors_per_s"] / small_single[op], 2)
+            extras["batched_short_m"][f"k{kk}"] = br
+        ps.close()
+        del Sm, ps
         extras["wide_fp64_small"] = small_fp64_flushed(pkg, dev)
         # least squares by CGLS on the same matrix: one SpMV + one SpVTM + vector updates per iteration
         bl = torch.rand(m, generator=g, device=dev) * 2 - 1
@@ -705,6 +726,10 @@ def run_ours(args):
         extras["atomic_scatter" if blocks else "row_blocks"] = dict(
             time_pair_gbs(pkg, pa, m, n, nnz, "csc", max(20, args.steps // 5)),
             blocks=pinfo["row_blocks"], widest_window=pinfo["row_block_window"])
+        if not blocks and pinfo["row_blocks"]:  # 8-vector SpMV passes over the row-sorted copy
+            brb = batched_rate(pkg, pa, m, n, nnz, 8, max(10, args.steps // 40), ops=("spmv",))["spmv"]
+            brb["vs_single_vector"] = round(brb["vectors_per_s"] / single["spmv"], 2)
+            extras["row_blocks"]["batched_k8_spmv"] = brb
         pa.close()
         vb = A.vals.to(torch.bfloat16)
         pb = pkg.Plan(m, n, A.ptr, A.idx, vb, layout="csc", vec_dtype=torch.float32, flags=order | blocks)

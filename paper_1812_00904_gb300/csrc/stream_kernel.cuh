@@ -869,15 +869,25 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         auto heads_of = [&](int i) -> uint32_t {
                             return (word_of(i) >> (((g + NG * i) & 3) << 3)) & 0xFFu;
                         };
-                        // heads of the tile before virtual lane i (the single-vector pass's base)
+                        // heads of the tile before virtual lane i (the single-vector pass's base): the
+                        // tile's heads before the step, the step's words before virtual lane i's word
+                        // and the bits of that word below the virtual lane's byte
                         const int cbs = __shfl_sync(FULL, cnt_ex, stp << 3);
-                        auto base_of = [&](int i) -> int {
+                        auto base_of = [&](int i, const int (&pre)[8]) -> int {
                             const int v = g + NG * i;
-                            int pre = 0;
+                            int pw = pre[(NG * i) >> 2];
+                            if constexpr (NG > 4) {
+                                if (((g + NG * i) >> 2) != ((NG * i) >> 2)) pw = pre[((NG * i) >> 2) + 1];
+                            }
+                            return cbs + pw + __popc(word_of(i) & ((1u << ((v & 3) << 3)) - 1u));
+                        };
+                        auto word_prefix = [&](int (&pre)[8]) {
+                            int a = 0;
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                if (j < (v >> 2)) pre += __popc(w[j]);
-                            return cbs + pre + __popc(word_of(i) & ((1u << ((v & 3) << 3)) - 1u));
+                            for (int j = 0; j < 8; ++j) {
+                                pre[j] = a;
+                                a += __popc(w[j]);
+                            }
                         };
                         // products of virtual lane i's 8 positions in position order (+0 outside the tile)
                         auto products = [&](int i, AT (&pe)[8]) {
@@ -963,6 +973,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         // before its first head (F); segments closing at its later heads are emitted
                         // here, from the lane's scratch of the values that close at each position
                         AT T[VL], F[VL];
+                        int pre[8];
+                        word_prefix(pre);
 #pragma unroll
                         for (int i = 0; i < VL; ++i) {
                             const uint32_t hb = heads_of(i);
@@ -984,7 +996,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                 if (act && rem) {
                                     const int p0 = (stp << 8) + ((g + NG * i) << 3);
                                     XT *o = static_cast<XT *>(p.vout[bv]);
-                                    int col = FAST ? i0 + base_of(i) : 0;
+                                    int col = FAST ? i0 + base_of(i, pre) : 0;
                                     while (rem) {  // a later head: the segment lies inside the virtual lane
                                         const int e = __ffs(rem) - 1;
                                         col = FAST ? col + 1 : col_search(p0 + e - 1);
@@ -1002,6 +1014,8 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         for (int lv = 0; lv < 5; ++lv) {
                             const int d = 1 << lv;
                             if (lv > 0) ok &= ok << (d >> 1);
+                            if (ok == 0u) break;  // (warp-uniform) no virtual lane adds at this level or later
+                            const unsigned okg = ok >> g;  // bit NG i: virtual lane g + NG i adds
                             if (d < NG) {
                                 // from lane group (g - d) mod NG: its sum of the same i, or of i - 1
                                 // when the distance wraps past group NG - 1
@@ -1013,12 +1027,12 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                     rv[i] = __shfl_sync(FULL, wsrc ? (i > 0 ? T[i > 0 ? i - 1 : 0] : AT(0)) : T[i], src);
 #pragma unroll
                                 for (int i = 0; i < VL; ++i)
-                                    if ((ok >> (g + NG * i)) & 1u) T[i] = T[i] + rv[i];
+                                    if ((okg >> (NG * i)) & 1u) T[i] = T[i] + rv[i];
                             } else {
                                 const int dd = d / NG;
 #pragma unroll
                                 for (int i = VL - 1; i >= dd; --i)
-                                    if ((ok >> (g + NG * i)) & 1u) T[i] = T[i] + T[i - dd];
+                                    if ((okg >> (NG * i)) & 1u) T[i] = T[i] + T[i - dd];
                             }
                         }
                         // open sum at the end of virtual lane v - 1 (0 for v = 0)
@@ -1047,7 +1061,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                 const AT lead = Tex[i] + (before ? AT(0) : cc);
                                 const AT val = F[i] + lead;
                                 const int e = __ffs(hb) - 1;
-                                emit(FAST ? i0 + base_of(i) : col_search((stp << 8) + (v << 3) + e - 1), bv, val);
+                                emit(FAST ? i0 + base_of(i, pre) : col_search((stp << 8) + (v << 3) + e - 1), bv, val);
                             }
                         }
                         chi[0] = __shfl_sync(FULL, T[VL - 1], (NG - 1) * VL + bv);

@@ -351,6 +351,16 @@ def wide_fp32_large(seed: int = 1, device="cuda", scale: float = 1.0, value_dtyp
                         value_dtype or torch.float32, "wide_csc_m20000_n5000000_fp32", scale)
 
 
+def wide_fp32_short(m: int = 2000, seed: int = 5, device="cuda", scale: float = 0.25) -> SparseMatrix:
+    """The recipe of wide_fp32_large with a short dimension of m rows (2,000 by default), so that
+    8 short vectors (m x 8 x 4 B) fit in one SM's shared memory; ``scale`` of the 5M columns
+    (a quarter by default: about 50M nonzeros)."""
+    import torch
+
+    return _large_torch("csc", 5_000_000, m, 2.0, 200e6, 50, 0.5, seed, device, torch.float32,
+                        f"wide_csc_m{m}_n5000000_fp32", scale)
+
+
 def tall_fp32_large(seed: int = 2, device="cuda", scale: float = 1.0, value_dtype=None) -> SparseMatrix:
     """m=10,000,000 x n=2,000 tall CSR, FP32 values, about 150M nonzeros."""
     import torch
