@@ -2,6 +2,8 @@
 // overlap-zone set-up of Sec. IV-B (needLeft, needRight, leftGroupEnd,
 // rightGroup, leftGroup, procsOnLeft, procsOnRight), and the merge-order tiles
 // each chunk streams through shared memory.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace gbk {
@@ -468,67 +470,158 @@ int stream_processors(int ntiles, int T, int nnz, int ctas, int C, int32_t *nzb)
 // r = 256 t + 32a + 8c + e asks for bank (4a + c + 4e) mod 32, one-to-one over the lanes
 // of the first two patterns and over the groups of the third; with 8-byte words (16 banks)
 // for ((r & 31) + ((r >> 5) & 7)) mod 16, one-to-one over each half of the lanes of the
-// first two.  One thread per segment: its
-// nonzeros are pooled by bank; every position, in order, takes a nonzero of the bank it
-// asks for while that pool lasts, else one of the fullest pool.  Within a bank the stored
-// order is kept.  Each thread reads and writes only its clamped range [s, e), so a
-// malformed ptr (an unvalidated plan) stays in bounds.
+// first two.
+//
+// One warp per segment: a position asking bank b is served by a nonzero of bank b when it is
+// among the first cnt[b] positions of the segment asking b (cnt[b]: the segment's nonzeros of
+// bank b), which serves as many positions as the pools allow; the positions left over take, in
+// order, the nonzeros left over, dealt round the banks (the first left-over nonzero of every
+// bank that has one, in bank order, then the second, ...), so that neighbouring left-over
+// positions differ in bank.  Within a bank the stored order is kept.  The warp passes over the
+// segment in chunks of 32 (lane = position or nonzero): the counts; the served positions'
+// lists (per bank, in order) and the overflow list, in slots[s ..); then every nonzero to its
+// position.  Every access stays in the segment's clamped range [s, e), so a malformed ptr (an
+// unvalidated plan) stays in bounds.
+__device__ __forceinline__ int bank_asked(int r, int nbm) {
+    return nbm == 31 ? (4 * ((r >> 5) & 7) + ((r >> 3) & 3) + 4 * (r & 7)) & 31 : ((r & 31) + ((r >> 5) & 7)) & nbm;
+}
+
+constexpr int BO_WARPS = 8;
+constexpr unsigned FULL = 0xffffffffu;
+
+// Segment [s, e) (at least 2 nonzeros) by the whole warp; run: this warp's 32 shared counters.
 template <typename W>
-__global__ void bank_order_kernel(const int32_t *__restrict__ ptr, int n_major, int nnz,
-                                  const int32_t *__restrict__ idx, const W *__restrict__ vals,
-                                  int32_t *__restrict__ oidx, W *__restrict__ ovals, int32_t *__restrict__ slots,
-                                  int T, int nbm) {
-    const long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (c >= n_major) return;
-    const int s = min(max(ptr[c], 0), nnz);
-    const int e = min(max(ptr[c + 1], s), nnz);
-    if (e - s <= 1) {
-        if (e > s) {
-            oidx[s] = idx[s];
-            ovals[s] = vals[s];
+__device__ void bank_order_segment(int s, int e, const int32_t *__restrict__ idx, const W *__restrict__ vals,
+                                int32_t *__restrict__ oidx, W *__restrict__ ovals, int32_t *__restrict__ slots, int T,
+                                int nbm, int *run) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int len = e - s;
+    const int r0 = s % T;
+    // ---- per-bank counts: nonzeros (cnt) and positions asking (ask); lane b holds bank b's
+    run[lane] = 0;
+    __syncwarp();
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        const int b = q < len ? (idx[s + q] & nbm) : 32 + lane;  // past the end: a bank of its own
+        const unsigned peers = __match_any_sync(FULL, b);
+        if (q < len && (peers & lt) == 0u) run[b] += __popc(peers);
+        __syncwarp();
+    }
+    const int cnt = run[lane];
+    __syncwarp();
+    run[lane] = 0;
+    __syncwarp();
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        const int b = q < len ? bank_asked((r0 + q) % T, nbm) : 32 + lane;
+        const unsigned peers = __match_any_sync(FULL, b);
+        if (q < len && (peers & lt) == 0u) run[b] += __popc(peers);
+        __syncwarp();
+    }
+    const int ask = run[lane];
+    // served per bank and where its served positions start
+    const int served = min(cnt, ask), left = cnt - served;
+    int off = served;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, off, d);
+        if (lane >= d) off += o;
+    }
+    const int total_served = __shfl_sync(FULL, off, 31);
+    off -= served;  // exclusive
+    // ---- positions: served ones into their bank's list, the others into the overflow list
+    __syncwarp();
+    run[lane] = 0;
+    __syncwarp();
+    int ovf = 0;
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        const bool in = q < len;
+        const int b = in ? bank_asked((r0 + q) % T, nbm) : 32 + lane;
+        const unsigned peers = __match_any_sync(FULL, b);
+        const int bb = in ? b : 0;
+        const int rank = run[bb] + __popc(peers & lt);
+        const int cb = __shfl_sync(FULL, cnt, bb);  // (every lane takes part in the shuffles)
+        const int ob = __shfl_sync(FULL, off, bb);
+        const bool srv = in && rank < cb;
+        const unsigned om = __ballot_sync(FULL, in && !srv);
+        if (srv) {
+            slots[s + ob + rank] = s + q;
+        } else if (in) {
+            const int t = total_served + ovf + __popc(om & lt);
+            if (t < len) slots[s + t] = s + q;
         }
-        return;
+        __syncwarp();
+        if (in && (peers & lt) == 0u) run[b] += __popc(peers);
+        ovf += __popc(om);
+        __syncwarp();
     }
-    int cnt[32], off[32], used[32];
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-        cnt[b] = 0;
-        used[b] = 0;
-    }
-    for (int j = s; j < e; ++j) ++cnt[idx[j] & nbm];
-    int o = 0;
-#pragma unroll
-    for (int b = 0; b < 32; ++b) {
-        off[b] = o;
-        o += cnt[b];
-    }
-    // the bank of every position; the positions given to bank b are listed in order at
-    // slots[s + off[b] ..]
-    int r = s % T;
-    for (int q = s; q < e; ++q) {
-        int b = nbm == 31 ? (4 * ((r >> 5) & 7) + ((r >> 3) & 3) + 4 * (r & 7)) & 31 : ((r & 31) + ((r >> 5) & 7)) & nbm;
-        if (used[b] == cnt[b]) {
-            int left = -1;
-            for (int k = 0; k <= nbm; ++k) {
-                if (cnt[k] - used[k] > left) {
-                    left = cnt[k] - used[k];
-                    b = k;
+    // ---- every nonzero to its position
+    run[lane] = 0;
+    __syncwarp();
+    for (int base = 0; base < len; base += 32) {
+        const int q = base + lane;
+        const bool in = q < len;
+        const int32_t ix = in ? idx[s + q] : 0;
+        const int b = in ? (ix & nbm) : 32 + lane;
+        const unsigned peers = __match_any_sync(FULL, b);
+        const int bb = in ? b : 0;
+        const int rank = run[bb] + __popc(peers & lt);
+        const int sv = __shfl_sync(FULL, served, bb);
+        const int o = __shfl_sync(FULL, off, bb);
+        const bool lo = in && rank >= sv;  // a left-over nonzero, number jj of its bank
+        const int jj = rank - sv;
+        int k = o + rank;
+        if (__any_sync(FULL, lo)) {
+            // its place in the round of the banks: every bank's first min(left, jj) left-overs,
+            // then those of the banks before it with more than jj (at most one left-over per
+            // bank: the banks before it that have one)
+            int before;
+            if (__ballot_sync(FULL, left > 1) == 0u) {
+                before = __popc(__ballot_sync(FULL, left > 0) & ((1u << bb) - 1u));
+            } else {
+                before = 0;
+                for (int b2 = 0; b2 <= nbm; ++b2) {
+                    const int l2 = __shfl_sync(FULL, left, b2);
+                    before += min(l2, max(jj, 0)) + ((b2 < bb && l2 > jj) ? 1 : 0);
                 }
             }
+            if (lo) k = total_served + before;
         }
-        slots[s + off[b] + used[b]] = q;
-        ++used[b];
-        if (++r == T) r = 0;
+        if (in) {
+            const int dst = (k >= 0 && k < len) ? slots[s + k] : -1;
+            if (dst >= s && dst < e) {
+                oidx[dst] = ix;
+                ovals[dst] = vals[s + q];
+            }
+        }
+        __syncwarp();
+        if (in && (peers & lt) == 0u) run[b] += __popc(peers);
+        __syncwarp();
     }
-#pragma unroll
-    for (int b = 0; b < 32; ++b) used[b] = 0;
-    for (int j = s; j < e; ++j) {
-        const int b = idx[j] & nbm;
-        const int q = slots[s + off[b] + used[b]];
-        ++used[b];
-        if (q >= s && q < e) {
-            oidx[q] = idx[j];
-            ovals[q] = vals[j];
+    __syncwarp();
+}
+
+template <typename W>
+__global__ void __launch_bounds__(BO_WARPS * 32) bank_order_kernel(const int32_t *__restrict__ ptr, int n_major,
+                                                                   int nnz, const int32_t *__restrict__ idx,
+                                                                   const W *__restrict__ vals,
+                                                                   int32_t *__restrict__ oidx, W *__restrict__ ovals,
+                                                                   int32_t *__restrict__ slots, int T, int nbm) {
+    __shared__ int sh_run[BO_WARPS][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long nw = (long)gridDim.x * BO_WARPS;
+    for (long c = (long)blockIdx.x * BO_WARPS + wib; c < n_major; c += nw) {
+        const int s = min(max(ptr[c], 0), nnz);
+        const int e = min(max(ptr[c + 1], s), nnz);
+        if (e - s == 1) {
+            if (lane == 0) {
+                oidx[s] = idx[s];
+                ovals[s] = vals[s];
+            }
+        } else if (e - s > 1) {
+            bank_order_segment(s, e, idx, vals, oidx, ovals, slots, T, nbm, sh_run[wib]);
         }
     }
 }
@@ -537,17 +630,19 @@ cudaError_t launch_bank_order(const int32_t *ptr, int n_major, int nnz, const in
                               int val_bytes, int32_t *oidx, void *ovals, int32_t *slots, int T, int banks,
                               cudaStream_t s) {
     if (n_major <= 0 || nnz <= 0) return cudaSuccess;
-    const int grid = (n_major + 127) / 128;
+    if (banks != 16 && banks != 32) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long>(((long)n_major + BO_WARPS - 1) / BO_WARPS, 152L * 64);
     const int nbm = banks - 1;
+    const int tb = BO_WARPS * 32;
     if (val_bytes == 8)
-        bank_order_kernel<uint64_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint64_t *>(vals),
-                                                         oidx, static_cast<uint64_t *>(ovals), slots, T, nbm);
+        bank_order_kernel<uint64_t><<<grid, tb, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint64_t *>(vals),
+                                                        oidx, static_cast<uint64_t *>(ovals), slots, T, nbm);
     else if (val_bytes == 4)
-        bank_order_kernel<uint32_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint32_t *>(vals),
-                                                         oidx, static_cast<uint32_t *>(ovals), slots, T, nbm);
+        bank_order_kernel<uint32_t><<<grid, tb, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint32_t *>(vals),
+                                                        oidx, static_cast<uint32_t *>(ovals), slots, T, nbm);
     else
-        bank_order_kernel<uint16_t><<<grid, 128, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint16_t *>(vals),
-                                                         oidx, static_cast<uint16_t *>(ovals), slots, T, nbm);
+        bank_order_kernel<uint16_t><<<grid, tb, 0, s>>>(ptr, n_major, nnz, idx, static_cast<const uint16_t *>(vals),
+                                                        oidx, static_cast<uint16_t *>(ovals), slots, T, nbm);
     return cudaGetLastError();
 }
 
