@@ -297,6 +297,20 @@ spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, 
                          const float *vals, const float *x, float *y, void *stream);
 
 /*
+ * spmv_pair -- y = A x (Sec. III) and u = v^T A (Sec. IV-A) for independent x and v in one
+ * call: the paper's SpMV-SpVTM pair (Sec. V) where the second product does not consume the
+ * first's result.  No counterpart in the paper beyond the two products.
+ *   x (n), y (m), v (m), u (n): vectors of the plan's vector type, each on the device (16-byte
+ *   aligned) or in host memory (pinned or pageable); y and u are overwritten
+ * With device pointers only, the SpMV then the SpVTM run on `stream`, asynchronously.  Otherwise
+ * the library stages the host vectors through its own device buffers on `stream` and on a copy
+ * stream of its own: the copy of x to the device overlaps the SpVTM kernels and the copy of u to
+ * the host overlaps the SpMV kernels, and the call returns after y and u have landed (work queued
+ * on `stream` before the call completes first).  Errors as for spmv and spvtm.
+ */
+spmv_status spmv_pair(spmv_plan_t plan, const void *x, void *y, const void *v, void *u, void *stream);
+
+/*
  * spmv_normal -- u = A^T (A x), the normal-equation operator of least squares:
  * one SpMV (Sec. III) whose result feeds one SpVTM (Sec. IV-A), the pairing the
  * paper measures (Sec. V) with the SpVTM consuming the SpMV's output.

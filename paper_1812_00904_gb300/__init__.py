@@ -16,7 +16,7 @@ from ._lib import (SPMV_BF16, SPMV_CSC_WIDE, SPMV_CSR_TALL, SPMV_F16, SPMV_F32, 
                    SPMV_PLAN_ROW_BLOCKS, SPMV_PLAN_SHORT_IN_GLOBAL, SpmvError)
 
 __all__ = [
-    "spmv_plan", "spmv_plan_ex", "spmv_plan_coo", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm",
+    "spmv_plan", "spmv_plan_ex", "spmv_plan_coo", "spmv_plan_destroy", "spmv_plan_info", "spmv_plan_chunks", "spmv", "spvtm", "spmv_pair",
     "spmv_batch", "spmv_dvalues", "spmv_noalloc", "spmv_normal", "spmv_cgls", "spmv_check", "spmv_plan_export", "spmv_profile_read", "spmv_profile_reset", "spmv_profile_enable", "spmv_last_error",
     "spmv_version", "serve_create", "serve_register", "serve_register_host", "serve_submit", "serve_poll",
     "serve_wait", "serve_stats", "serve_destroy", "Plan", "SparseMatVec", "sparse_matvec", "SpmvError",
@@ -109,6 +109,12 @@ def spmv(plan, x, y, stream=None):
 
 def spvtm(plan, v, u, stream=None):
     _lib.call("spvtm", plan, _addr(v), _addr(u), _stream(stream))
+
+
+def spmv_pair(plan, x, y, v, u, stream=None):
+    """y = A x and u = v^T A for independent x and v in one call (host vectors' copies overlap
+    the other product's kernels)."""
+    _lib.call("spmv_pair", plan, _addr(x), _addr(y), _addr(v), _addr(u), _stream(stream))
 
 
 def spmv_batch(plan, op, k, inp, ld_in, out, ld_out, stream=None):

@@ -88,6 +88,7 @@ SIGNATURES = {
     "spmv_plan_chunks": (_I32, [_P, ctypes.POINTER(spmv_chunk_t), _I32]),
     "spmv": (_I32, [_P, _P, _P, _P]),
     "spvtm": (_I32, [_P, _P, _P, _P]),
+    "spmv_pair": (_I32, [_P, _P, _P, _P, _P, _P]),
     "spmv_batch": (_I32, [_P, _I32, _I32, _P, _I64, _P, _I64, _P]),
     "spmv_dvalues": (_I32, [_P, _P, _P, _P, _P]),
     "spmv_check": (_I32, [_P, _P]),

@@ -412,6 +412,11 @@ void plan_free(spmv_plan_s *p) {
     if (p->ws2) cudaFree(p->ws2);
     if (p->hin) cudaFree(p->hin);
     if (p->hout) cudaFree(p->hout);
+    if (p->hv) cudaFree(p->hv);
+    if (p->hu) cudaFree(p->hu);
+    if (p->ev_x) cudaEventDestroy(p->ev_x);
+    if (p->ev_u) cudaEventDestroy(p->ev_u);
+    if (p->cstream) cudaStreamDestroy(p->cstream);
     if (p->hg) cudaFree(p->hg);
     if (p->ynorm) cudaFree(p->ynorm);
     if (p->owned_ptr) cudaFree(p->owned_ptr);
@@ -815,6 +820,71 @@ spmv_status spvtm(spmv_plan_t p, const void *v, void *u, void *stream) {
     return with_staging(p, v, (size_t)p->m * p->sx, u, (size_t)p->n * p->sx, s, [&](const void *dv, void *du) {
         return run_op(p, SPMV_OP_VTA, 1, &dv, &du, s);
     });
+}
+
+// The two products of a pair with host vectors: x's copy to the device runs on the plan's
+// copy stream while the SpVTM kernels run on `s`, and u's copy to the host runs there while the
+// SpMV kernels run.  Both streams are drained before returning, whatever happened.
+static spmv_status pair_staged(spmv_plan_s *p, const void *x, void *y, const void *v, void *u, PtrKind kx,
+                               PtrKind ky, PtrKind kv, PtrKind ku, cudaStream_t s) {
+    const size_t cap = (size_t)std::max(p->m, p->n) * p->sx + 16;
+    const size_t xb = (size_t)p->n * p->sx, yb = (size_t)p->m * p->sx;
+    for (void **b : {&p->hin, &p->hout, &p->hv, &p->hu})
+        if (!*b) CUDA_TRY(cudaMalloc(b, cap));
+    if (!p->cstream) CUDA_TRY(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
+    if (!p->ev_x) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_x, cudaEventDisableTiming));
+    if (!p->ev_u) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_u, cudaEventDisableTiming));
+    cudaStream_t cs = p->cstream;
+    spmv_status st = SPMV_OK;
+    cudaError_t ce = cudaSuccess;
+    auto step = [&](cudaError_t e) {
+        if (ce == cudaSuccess && e != cudaSuccess) ce = e;
+        return ce == cudaSuccess;
+    };
+    const void *dx = x, *dv = v;
+    void *dy = ky == PK_HOST ? p->hout : y, *du = ku == PK_HOST ? p->hu : u;
+    // the copy stream starts after the work already queued on s (which may use the buffers)
+    step(cudaEventRecord(p->ev_u, s)) && step(cudaStreamWaitEvent(cs, p->ev_u, 0));
+    if (kx == PK_HOST && step(cudaMemcpyAsync(p->hin, x, xb, cudaMemcpyHostToDevice, cs)) &&
+        step(cudaEventRecord(p->ev_x, cs)))
+        dx = p->hin;
+    if (kv == PK_HOST && step(cudaMemcpyAsync(p->hv, v, yb, cudaMemcpyHostToDevice, s))) dv = p->hv;
+    if (ce == cudaSuccess) st = run_op(p, SPMV_OP_VTA, 1, &dv, &du, s);
+    if (st == SPMV_OK && ku == PK_HOST && step(cudaEventRecord(p->ev_u, s)) && step(cudaStreamWaitEvent(cs, p->ev_u, 0)))
+        step(cudaMemcpyAsync(u, p->hu, xb, cudaMemcpyDeviceToHost, cs));
+    if (st == SPMV_OK && kx == PK_HOST) step(cudaStreamWaitEvent(s, p->ev_x, 0));
+    if (st == SPMV_OK && ce == cudaSuccess) st = run_op(p, SPMV_OP_AX, 1, &dx, &dy, s);
+    if (st == SPMV_OK && ky == PK_HOST) step(cudaMemcpyAsync(y, p->hout, yb, cudaMemcpyDeviceToHost, s));
+    const cudaError_t e1 = cudaStreamSynchronize(cs), e2 = cudaStreamSynchronize(s);
+    if (st != SPMV_OK) return st;
+    step(e1);
+    step(e2);
+    if (ce != cudaSuccess)
+        return set_error(ce == cudaErrorMemoryAllocation ? SPMV_ERR_OOM : SPMV_ERR_CUDA,
+                         std::string("spmv_pair: ") + cudaGetErrorString(ce));
+    return SPMV_OK;
+}
+
+spmv_status spmv_pair(spmv_plan_t p, const void *x, void *y, const void *v, void *u, void *stream) {
+    if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto kind = [](const void *ptr, size_t bytes) { return (bytes == 0 && !ptr) ? PK_DEVICE : classify(ptr); };
+    const size_t xb = (size_t)p->n * p->sx, yb = (size_t)p->m * p->sx;
+    const PtrKind kx = kind(x, xb), ky = kind(y, yb), kv = kind(v, yb), ku = kind(u, xb);
+    if (kx == PK_BAD || ky == PK_BAD || kv == PK_BAD || ku == PK_BAD)
+        return set_error(SPMV_ERR_INVALID_ARG, "null vector pointer");
+    const void *ptrs[4] = {x, y, v, u};
+    const PtrKind kinds[4] = {kx, ky, kv, ku};
+    for (int i = 0; i < 4; ++i)
+        if (kinds[i] == PK_DEVICE && ptrs[i] && !aligned16(ptrs[i]))
+            return set_error(SPMV_ERR_INVALID_ARG, "device vector pointers must be 16-byte aligned");
+    if (kx == PK_DEVICE && ky == PK_DEVICE && kv == PK_DEVICE && ku == PK_DEVICE) {
+        spmv_status st = run_op(p, SPMV_OP_AX, 1, &x, &y, s);
+        if (st != SPMV_OK) return st;
+        return run_op(p, SPMV_OP_VTA, 1, &v, &u, s);
+    }
+    std::lock_guard<std::mutex> lk(p->host_mu);
+    return pair_staged(p, x, y, v, u, kx, ky, kv, ku, s);
 }
 
 spmv_status spmv_batch(spmv_plan_t p, int32_t op, int32_t k, const void *in, int64_t ld_in, void *out, int64_t ld_out,

@@ -62,6 +62,11 @@ struct spmv_plan_s {
     // staging buffers for host-pointer calls (allocated on first use)
     std::mutex host_mu;
     void *hin = nullptr, *hout = nullptr, *hg = nullptr;
+    // spmv_pair with host vectors: device copies of v and u, and a copy stream of the plan's own
+    // with its two events (made on first use)
+    void *hv = nullptr, *hu = nullptr;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_x = nullptr, ev_u = nullptr;
     void *ynorm = nullptr;  // A x of spmv_normal when the caller passes no buffer
     void *owned_ptr = nullptr;  // pointer array built by spmv_plan_coo (the other arrays stay borrowed)
     void *owned_nz = nullptr;   // plan-owned idx and vals: bank order, or triples sorted by spmv_plan_coo

@@ -1,0 +1,82 @@
+"""spmv_pair: y = A x and u = v^T A for independent x and v in one call, with device vectors
+(two ordered launches) and with host vectors (staged, the transfers of each product overlapping
+the other's kernels).  Results must match the FP64 oracle and the separate calls (bit for bit
+in the segmented direction, whose sums are formed in a fixed order)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+import paper_1812_00904_gb300 as pkg  # noqa: E402
+from paper_1812_00904_gb300 import _lib  # noqa: E402
+from gpu_util import DEV, assert_close, dev_vec, host_of, make_plan  # noqa: E402
+
+
+def _case(layout):
+    m, n = (2000, 60_000) if layout == "csc" else (60_000, 2000)
+    A = synth.random_matrix(m, n, layout, density=0.004, seed=71)
+    plan, stored = make_plan(A, torch.float32)
+    x = synth.uniform_vector(n, 72).astype(np.float32)
+    v = synth.uniform_vector(m, 73).astype(np.float32)
+    return A, plan, stored, x, v
+
+
+def _check(stored, x, v, y, u, what):
+    xs, vs = x.astype(np.float64), v.astype(np.float64)
+    assert_close(np.asarray(y, np.float64), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), 1e-5, f"{what} y")
+    assert_close(np.asarray(u, np.float64), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), 1e-5, f"{what} u")
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+@pytest.mark.parametrize("where", ["device", "pinned", "pageable", "mixed"])
+def test_pair_matches_the_oracle_and_the_separate_calls(layout, where):
+    A, plan, stored, x, v = _case(layout)
+    xd, vd = dev_vec(x, torch.float32), dev_vec(v, torch.float32)
+    ref_y, ref_u = plan.spmv(xd), plan.spvtm(vd)
+    torch.cuda.synchronize()
+    if where == "device":
+        xa, va = xd, vd
+        ya, ua = torch.empty(A.m, device=DEV), torch.empty(A.n, device=DEV)
+    else:
+        pin = where == "pinned"
+        mk = (lambda a: torch.from_numpy(a).pin_memory()) if pin else (lambda a: torch.from_numpy(a.copy()))
+        xa, va = mk(x), mk(v)
+        ya = torch.full((A.m,), np.nan).float()
+        ua = torch.full((A.n,), np.nan).float()
+        if pin:
+            ya, ua = ya.pin_memory(), ua.pin_memory()
+        if where == "mixed":  # x and u on the host, v and y on the device
+            va, ya = vd, torch.empty(A.m, device=DEV)
+    pkg.spmv_pair(plan.handle, xa, ya, va, ua)
+    if where == "device":
+        torch.cuda.synchronize()
+    # host results have landed when the call returns
+    y, u = host_of(ya), host_of(ua)
+    _check(stored, x, v, y, u, where)
+    seg = u if layout == "csc" else y
+    seg_ref = host_of(ref_u if layout == "csc" else ref_y)
+    assert np.array_equal(seg, seg_ref), "segmented direction differs from the separate call"
+    plan.check()
+    plan.close()
+
+
+def test_pair_repeated_calls_and_errors():
+    A, plan, stored, x, v = _case("csc")
+    xa, va = torch.from_numpy(x).pin_memory(), torch.from_numpy(v).pin_memory()
+    ya, ua = torch.empty(A.m).pin_memory(), torch.empty(A.n).pin_memory()
+    for rep in range(5):  # the staging buffers, copy stream and events are reused
+        xa.mul_(-1.0)
+        pkg.spmv_pair(plan.handle, xa, ya, va, ua)
+        _check(stored, xa.numpy(), v, ya.numpy(), ua.numpy(), f"repeat {rep}")
+    lib = _lib.load()
+    assert lib.spmv_pair(plan.handle, None, ya.data_ptr(), va.data_ptr(), ua.data_ptr(), None) == _lib.SPMV_ERR_INVALID_ARG
+    yd = torch.empty(A.m + 4, device=DEV)
+    assert lib.spmv_pair(plan.handle, xa.data_ptr(), yd.data_ptr() + 4, va.data_ptr(), ua.data_ptr(),
+                         None) == _lib.SPMV_ERR_INVALID_ARG  # misaligned device vector
+    assert "aligned" in lib.spmv_last_error().decode()
+    plan.check()
+    plan.close()
