@@ -135,7 +135,7 @@ typedef struct {
     int32_t zones;             /* z, overlap zones (Sec. II), z <= P-1 */
     int32_t max_zone_size;     /* V = max |S_k| (Sec. IV-A) */
     int32_t short_on_chip;     /* 1 if the short vector lives in shared memory */
-    int32_t batch_width;       /* vectors per pass of spmv_batch (1..8) */
+    int32_t batch_width;       /* vectors per pass of the accumulating direction of spmv_batch (1..8) */
     int64_t max_chunk_nnz, min_chunk_nnz;
     double imbalance;          /* Delta = P (max - min) / Z (Sec. VI), 0 when Z = 0 */
     int64_t workspace_bytes;   /* device bytes owned by the plan */
@@ -222,15 +222,19 @@ spmv_status spmv(spmv_plan_t plan, const void *x, void *y, void *stream);
 spmv_status spvtm(spmv_plan_t plan, const void *v, void *u, void *stream);
 
 /*
- * spmv_batch -- k products with one pass over the matrix per group of
- * batch_width vectors (spmv_plan_info).  op = SPMV_OP_AX: Y = A X, vector b of
- * X at in + b*ld_in (length n), of Y at out + b*ld_out (length m);
+ * spmv_batch -- k products of the same kind.  op = SPMV_OP_AX: Y = A X, vector b
+ * of X at in + b*ld_in (length n), of Y at out + b*ld_out (length m);
  * op = SPMV_OP_VTA: U^T = V^T A with lengths m in, n out.  ld in elements,
  * ld >= vector length and ld * element size a multiple of 16.  Device pointers
- * only.  1 <= k <= 4096.  Every vector's result equals its single-vector
- * product within the stated tolerances.  The paper multiplies one vector at a
- * time; the multi-vector form has no counterpart there (each vector's product
- * is the Sec. III / Sec. IV-A computation).
+ * only.  1 <= k <= 4096.  The segmented direction (SpVTM of a wide CSC plan,
+ * SpMV of a tall CSR one, and the SpMV of a plan with SPMV_PLAN_ROW_BLOCKS)
+ * streams the matrix once per 8 vectors, and every vector's result equals its
+ * single-vector product bit for bit, whatever k and the vector's place in the
+ * batch.  The accumulating direction runs batch_width vectors (spmv_plan_info)
+ * per pass; its results equal the single-vector products within the stated
+ * tolerances (floating-point atomic additions, in no fixed order).  The paper
+ * multiplies one vector at a time; the multi-vector form has no counterpart
+ * there (each vector's product is the Sec. III / Sec. IV-A computation).
  */
 spmv_status spmv_batch(spmv_plan_t plan, int32_t op, int32_t k, const void *in, int64_t ld_in,
                        void *out, int64_t ld_out, void *stream);
