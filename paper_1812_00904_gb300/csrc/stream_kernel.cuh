@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         chunk0 = gb * chunks_of(tq) + min(gb, tr) * (chunks_of(tq + 1) - chunks_of(tq));
     };
     auto tile_of = [&](int k) {  // tile of this warp's k-th tile of the block
+        if constexpr (!SEGM) return ta + warp + k * W;  // no carries: the block's tiles round-robin
         return k < cnt * C ? ta + (warp + (k / C) * W) * C + k % C : ta + nb * C + toff + (k - cnt * C);
     };
 
