@@ -433,15 +433,18 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             }
                     }
                 }
-                // head counts before every mask word
-                int incl = __popc(mw);
+                // head counts before every mask word (the scatter pass counts them step by step)
+                int cnt_ex = 0, htotal = 0;
+                if constexpr (MODE != MODE_SCATTER) {
+                    int incl = __popc(mw);
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const int v = __shfl_up_sync(FULL, incl, d);
-                    if (lane >= d) incl += v;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int v = __shfl_up_sync(FULL, incl, d);
+                        if (lane >= d) incl += v;
+                    }
+                    cnt_ex = incl - __popc(mw);
+                    htotal = __shfl_sync(FULL, incl, 31);
                 }
-                const int cnt_ex = incl - __popc(mw);
-                const int htotal = __shfl_sync(FULL, incl, 31);
 
                 // ---- DVALUES: 4 consecutive positions per lane, 128 per step
                 auto run_steps4 = [&](auto fast_tag) {
@@ -582,6 +585,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     const VT *vv = reinterpret_cast<const VT *>(val_s);
                     const uint32_t lane_le = FULL >> (31 - lane);  // bits 0..lane
                     const int nsteps = (rel_hi + 255) >> 8;
+                    int cbr = 0;  // segment starts of the tile before the step
                     for (int stp = 0; stp < nsteps; ++stp) {
                         const int s0 = stp << 8;
                         // segment-start words of the step (positions s0 + 32e .. s0 + 32e + 31)
@@ -597,7 +601,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                     if ((stp << 3) + e >= p.mwp) w[e] = 0u;
                             }
                         }
-                        const int cb = __shfl_sync(FULL, cnt_ex, stp << 3);  // segment starts before the step
+                        const int cb = cbr;
                         // all loads of the step first (independent), then the additions
                         int row[8];
                         AT a[8];
@@ -645,6 +649,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                                 ce[e] = FAST ? pre + __popc(w[e] & lane_le) : col_search(s0 + (e << 5) + lane);
                                 pre += __popc(w[e]);
                             }
+                            cbr = pre - i0;  // (a step without segment starts leaves it as it was)
                         }
 #pragma unroll
                         for (int b = 0; b < KB; ++b) {
