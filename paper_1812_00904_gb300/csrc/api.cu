@@ -93,6 +93,8 @@ StreamParams base_params(const spmv_plan_s *p) {
     sp.masks = p->masks;
     sp.ntiles = p->ntiles;
     sp.mwp = p->mwp;
+    sp.pfx = p->pfx;
+    sp.mwq = p->mwq;
     sp.slots = p->S;
     sp.x_cap = p->x_cap;
     sp.tile_cap = p->T;
@@ -116,8 +118,11 @@ SlotGeom slot_geom(const spmv_plan_s *p, int mode, int kbt) {
     g.off_val = (int)align_up((size_t)p->T * 4, 128);
     g.off_mask = g.off_val + (int)align_up((size_t)p->T * p->sv, 128);
     g.off_x = g.off_mask + (int)align_up((size_t)p->mwp * 4, 16);
-    const int nx = (mode == MODE_SEGDOT || mode == MODE_VSEG) ? 0 : mode == MODE_DVALUES ? 1 : kbt;
-    g.off_hdr = (int)align_up((size_t)g.off_x + (size_t)nx * p->x_cap * p->sx, 16);  // 32-byte tile header
+    const bool seg = mode == MODE_SEGDOT || mode == MODE_VSEG;
+    const int nx = seg ? 0 : mode == MODE_DVALUES ? 1 : kbt;
+    // the segmented modes stage the tile's head-count prefix table where the others stage windows
+    const size_t xbytes = seg ? align_up((size_t)p->mwq * 2, 16) : (size_t)nx * p->x_cap * p->sx;
+    g.off_hdr = (int)align_up((size_t)g.off_x + xbytes, 16);  // 32-byte tile header
     g.bytes = (int)align_up((size_t)g.off_hdr + 32, 128);
     return g;
 }
@@ -152,6 +157,7 @@ void set_geometry(const spmv_plan_s *p, LaunchArgs &a, int mode, int kbt, bool s
     a.sp.off_val = g.off_val;
     a.sp.off_mask = g.off_mask;
     a.sp.off_x = g.off_x;
+    a.sp.off_pfx = g.off_x;
     a.sp.off_hdr = g.off_hdr;
     a.smem = a.sp.vec_region_bytes + BAR_BYTES + W * p->S * g.bytes;
     a.grid = p->ctas;
@@ -557,6 +563,8 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     if (opts && (opts->chunk_tiles < 0 || opts->chunk_tiles > 64))
         return set_error(SPMV_ERR_INVALID_ARG, "chunk_tiles must lie in [0, 64]");
     p->mwp = (int)align_up((size_t)(p->T + 8 + 31) / 32, 4);
+    // prefix entries: one per mask word and the total, and at least one per word a step reads
+    p->mwq = (int)align_up((size_t)std::max(p->mwp + 1, 8 * ((p->T + 255) / 256)), 8);
     p->x_cap = (int)align_up((size_t)p->T / 4 + 16, 8);  // columns of a tile's window (fall back to global beyond)
     p->smem_max = smem_max;
     p->W = W;
@@ -683,6 +691,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     off = 0;
     const size_t o_meta = carve((size_t)(nt + 1) * sizeof(TileMeta));
     const size_t o_masks = carve((size_t)std::max(nt, 1) * p->mwp * 4);
+    const size_t o_pfx = carve((size_t)std::max(nt, 1) * p->mwq * 2);
     const size_t o_pz = carve((size_t)p->max_nproc * sizeof(ZoneDev));
     const size_t o_recl = carve(rec_bytes);
     const size_t o_recr = carve(rec_bytes);
@@ -700,6 +709,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
     char *w2 = static_cast<char *>(p->ws2);
     p->meta = reinterpret_cast<TileMeta *>(w2 + o_meta);
     p->masks = reinterpret_cast<uint32_t *>(w2 + o_masks);
+    p->pfx = reinterpret_cast<uint16_t *>(w2 + o_pfx);
     p->rec_left = w2 + o_recl;
     p->rec_right = w2 + o_recr;
     p->part = w2 + o_part;
@@ -712,7 +722,7 @@ spmv_status gbk::plan_create(spmv_plan_s **out, int64_t m, int64_t n, int64_t nn
         // execution tiles: bounds, first/last segments, owned end events; masks and descriptors
         CUDA_TRY(launch_tile_bounds(nt, p->T, (int)nnz, tnzb, s));
         CUDA_TRY(launch_chunks(p->pptr, p->n_major, (int)nnz, nt, tnzb, p->T, taux, s));
-        CUDA_TRY(launch_masks(p->pptr, taux, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->meta, s));
+        CUDA_TRY(launch_masks(p->pptr, taux, nt, (int)nnz, p->n_major, p->mwp, p->masks, p->mwq, p->pfx, p->meta, s));
         // the Sec. IV-B set-up over the processors (chunks) gives their overlap zones
         spmv_plan_s::ProcZones &pz = p->pz;
         pz.zones = reinterpret_cast<ZoneDev *>(w2 + o_pz);

@@ -131,7 +131,8 @@ spmv_status build_row_blocks(spmv_plan_s *p, int sms, cudaStream_t s) {
         const int mwp = (int)(((size_t)Tc + 8 + 31) / 32 + 3) / 4 * 4;
         // the window budget: what the segmented pass leaves beside 16 warps of staging slots
         const size_t slot = (size_t)p->S * (((size_t)Tc * 4 + 127) / 128 * 128 +
-                                            ((size_t)Tc * p->sv + 127) / 128 * 128 + (size_t)mwp * 4 + 160);
+                                            ((size_t)Tc * p->sv + 127) / 128 * 128 + (size_t)mwp * 4 +
+                                            ((size_t)p->mwq * 2 + 15) / 16 * 16 + 160);
         const size_t budget =
             (size_t)p->smem_max > BAR_BYTES + 16 * slot ? (size_t)p->smem_max - BAR_BYTES - 16 * slot : 0;
         const int64_t max_elems = (int64_t)(budget / p->sx);

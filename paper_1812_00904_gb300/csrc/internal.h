@@ -62,9 +62,11 @@ struct StreamParams {
     int32_t nnz, n_major, n_minor;
     const TileMeta *meta;    // ntiles + 1 entries
     const uint32_t *masks;   // per tile: mwp words of segment-start bits
-    int32_t ntiles, mwp;
+    const uint16_t *pfx;     // per tile: mwq entries, the segment starts before word j (j >= mwp: all of them)
+    int32_t ntiles, mwp, mwq;
     int32_t slot_bytes, vec_region_bytes, slots, x_cap;  // per-warp slot bytes, slots per warp, window elements
     int32_t tile_cap, off_val, off_mask, off_x, off_hdr;  // slot layout: indices at 0, values, masks, windows, header
+    int32_t off_pfx;         // segmented modes: the tile's head-count prefix table in the slot (at off_x)
     int32_t checked;         // 1: indices not validated by the plan, checked (clamped) on every step
     int32_t kb;              // vectors in this pass (<= KB template)
     const void *vin[KB_MAX]; // SCATTER: major vectors; SEGDOT: minor vectors; DVALUES: vin[0] minor, vin[1] major;
@@ -152,6 +154,6 @@ cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cu
 // Per tile: segment-start masks and the kernel's tile descriptors (needLeft / needRight of
 // every tile from its neighbours' first and last segments).
 cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles, int nnz, int n_major, int mwp,
-                         uint32_t *masks, TileMeta *meta, cudaStream_t s);
+                         uint32_t *masks, int mwq, uint16_t *pfx, TileMeta *meta, cudaStream_t s);
 
 }  // namespace gbk

@@ -385,7 +385,8 @@ cudaError_t launch_tile_bounds(int ntiles, int T, int nnz, int32_t *tile_nzb, cu
 // empty); bit 2 marks a tile in which an empty segment ends (then several
 // segments can start at one position and the kernels take their general path).
 __global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkAux *__restrict__ tiles, int ntiles, int nnz,
-                             int n_major, int mwp, uint32_t *__restrict__ masks, TileMeta *__restrict__ meta) {
+                             int n_major, int mwp, uint32_t *__restrict__ masks, int mwq, uint16_t *__restrict__ pfx,
+                             TileMeta *__restrict__ meta) {
     __shared__ uint32_t sm[8][32];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -406,6 +407,20 @@ __global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkAux *_
     dup = __any_sync(0xffffffffu, dup);
     __syncwarp();
     if (lane < mwp) masks[(size_t)t * mwp + lane] = sm[wib][lane];
+    // segment starts before each word (exclusive prefix over the tile's words; from word mwp on,
+    // all of the tile's), for the segmented passes
+    {
+        const int c = lane < mwp ? __popc(sm[wib][lane]) : 0;
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int j = lane; j < mwq; j += 32)  // (entry j < 32 is lane j's own)
+            pfx[(size_t)t * mwq + j] = static_cast<uint16_t>(j < 32 ? incl - c : total);
+    }
     if (lane == 0) {
         TileMeta m;
         m.nzb = d.nz_begin;
@@ -427,9 +442,9 @@ __global__ void masks_kernel(const int32_t *__restrict__ pptr, const ChunkAux *_
 }
 
 cudaError_t launch_masks(const int32_t *pptr, const ChunkAux *tiles, int ntiles, int nnz, int n_major, int mwp,
-                         uint32_t *masks, TileMeta *meta, cudaStream_t s) {
+                         uint32_t *masks, int mwq, uint16_t *pfx, TileMeta *meta, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
-    masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, tiles, ntiles, nnz, n_major, mwp, masks, meta);
+    masks_kernel<<<(ntiles + 7) / 8, 256, 0, s>>>(pptr, tiles, ntiles, nnz, n_major, mwp, masks, mwq, pfx, meta);
     return cudaGetLastError();
 }
 

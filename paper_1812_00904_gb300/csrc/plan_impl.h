@@ -27,6 +27,7 @@ struct spmv_plan_s {
     int ctas = 0, W = 0, T = 0, S = 0;  // W: most warps per CTA (each pass fits what shared memory holds)
     int W_info = 0;                       // warps of the single-vector scatter pass (spmv_plan_info)
     int mwp = 0, x_cap = 0, pptr_len = 0, smem_max = 0;  // masks words per tile, window elements per tile
+    int mwq = 0;                // entries per tile of the head-count prefix table (a multiple of 8)
     int chunk_tiles = 1;  // tiles per chunk of the streaming kernels' full rounds
     int bpc = 1;          // blocks (Sec. II ranges of whole tiles) each CTA runs in turn
     bool onchip = false;
@@ -44,6 +45,7 @@ struct spmv_plan_s {
     int32_t *err = nullptr;
     gbk::TileMeta *meta = nullptr;         // execution tiles (ntiles + 1)
     uint32_t *masks = nullptr;
+    uint16_t *pfx = nullptr;    // per tile: segment starts before each mask word (then the total)
     // Overlap zones among the processors of the streaming passes: the chunks of whole tiles
     // (contiguous Sec. II groups) every CTA's tile range is cut into.
     struct ProcZones {

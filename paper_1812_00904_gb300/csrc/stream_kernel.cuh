@@ -208,6 +208,11 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         c_src = reinterpret_cast<const unsigned char *>(p.masks);
         c_off = p.off_mask;
         c_len = p.ntiles * p.mwp;
+    } else if (SEGM && lane == 3) {  // the segmented modes: the tile's head-count prefix table
+        c_src = reinterpret_cast<const unsigned char *>(p.pfx);
+        c_off = p.off_pfx;
+        c_len = p.ntiles * p.mwq;
+        c_es = 2;
     } else if (lane >= 3) {
         const int b = lane - 3;
         c_src = static_cast<const unsigned char *>((MODE == MODE_DVALUES) ? p.vin[1] : p.vin[b < KB_MAX ? b : 0]);
@@ -230,6 +235,9 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
         if (lane == 2) {
             e0 = e.y * p.mwp;
             cnt = p.mwp;
+        } else if (SEGM && lane == 3) {
+            e0 = e.y * p.mwq;
+            cnt = p.mwq;
         } else if (lane >= 3) {
             e0 = xbase;
             cnt = (c_x && nxc <= p.x_cap) ? nxc : 0;
@@ -398,6 +406,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                 const unsigned char *val_s = slot + p.off_val;
                 const uint32_t *mask_s = reinterpret_cast<const uint32_t *>(slot + p.off_mask);
                 const XT *x_s = reinterpret_cast<const XT *>(slot + p.off_x);
+                const uint16_t *pfx_s = reinterpret_cast<const uint16_t *>(slot + p.off_pfx);  // segmented modes
                 const uint32_t mw = lane < p.mwp ? mask_s[lane] : 0u;
                 bool idx_bad = false;  // an index outside the short vector was met in this tile
 
@@ -433,9 +442,12 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             }
                     }
                 }
-                // head counts before every mask word (the scatter pass counts them step by step)
+                // head counts before every mask word: the segmented modes read them from the tile's
+                // prefix table, the scatter pass counts them step by step
                 int cnt_ex = 0, htotal = 0;
-                if constexpr (MODE != MODE_SCATTER) {
+                if constexpr (SEGM) {
+                    htotal = pfx_s[p.mwp];
+                } else if constexpr (MODE == MODE_DVALUES) {
                     int incl = __popc(mw);
 #pragma unroll
                     for (int d = 1; d < 32; d <<= 1) {
@@ -504,8 +516,9 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     constexpr bool WHOLE = decltype(full_tag)::value;
                     p0 = (stp << 8) + (lane << 3);
                     const int sh = (lane & 3) << 3;
-                    const uint32_t mwl = __shfl_sync(FULL, mw, p0 >> 5);
-                    const int cwl = __shfl_sync(FULL, cnt_ex, p0 >> 5);
+                    const int wi = p0 >> 5;  // the lane's mask word
+                    const uint32_t mwl = wi < p.mwp ? mask_s[wi] : 0u;
+                    const int cwl = pfx_s[wi];
                     hb = (mwl >> sh) & 0xFFu;
                     base = cwl + __popc(mwl & ((1u << sh) - 1u));
                     if constexpr (WHOLE) {
@@ -878,7 +891,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         // heads of the tile before virtual lane i (the single-vector pass's base): the
                         // tile's heads before the step, the step's words before virtual lane i's word
                         // and the bits of that word below the virtual lane's byte
-                        const int cbs = __shfl_sync(FULL, cnt_ex, stp << 3);
+                        const int cbs = pfx_s[stp << 3];
                         auto base_of = [&](int i, const int (&pre)[8]) -> int {
                             const int v = g + NG * i;
                             int pw = pre[(NG * i) >> 2];
