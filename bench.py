@@ -422,7 +422,7 @@ def serving_measurement(pkg, dev, seconds: float = 2.0, rates=(0.5, 0.8, 1.0)):
     mats, plans = [], []
     for sp in specs:
         A = synth.serving_matrix(sp, device=dev)
-        plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout=A.layout)
+        plan = pkg.Plan(A.m, A.n, A.ptr, A.idx, A.vals, layout=A.layout, flags=pkg.SPMV_PLAN_BANK_ORDER)
         mats.append(A)
         plans.append(plan)
     gen_s = time.time() - t0
