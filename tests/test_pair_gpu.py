@@ -80,3 +80,28 @@ def test_pair_repeated_calls_and_errors():
     assert "aligned" in lib.spmv_last_error().decode()
     plan.check()
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.bfloat16], ids=str)
+@pytest.mark.parametrize("flags", [0, pkg.SPMV_PLAN_ROW_BLOCKS, pkg.SPMV_PLAN_BANK_ORDER],
+                         ids=["stored", "row_blocks", "bank_order"])
+def test_pair_value_types_and_plan_copies(dtype, flags):
+    """Host-staged pairs on FP64 and BF16-value plans, and on plans that multiply their own
+    copies of the nonzeros (row-sorted blocks, bank order), against the FP64 oracle."""
+    from gpu_util import TOL, vec_dtype_for
+
+    A = synth.random_matrix(1500, 80_000, "csc", density=0.003, seed=81)
+    plan, stored = make_plan(A, dtype, flags=flags)
+    vt = vec_dtype_for(dtype)
+    x = synth.uniform_vector(A.n, 82)
+    v = synth.uniform_vector(A.m, 83)
+    xh = torch.from_numpy(x).to(vt).pin_memory()
+    vh = torch.from_numpy(v).to(vt).pin_memory()
+    yh = torch.empty(A.m, dtype=vt).pin_memory()
+    uh = torch.empty(A.n, dtype=vt).pin_memory()
+    pkg.spmv_pair(plan.handle, xh, yh, vh, uh)
+    xs, vs = xh.double().numpy(), vh.double().numpy()
+    assert_close(yh.double().numpy(), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), TOL[dtype], "pair y")
+    assert_close(uh.double().numpy(), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), TOL[dtype], "pair u")
+    plan.check()
+    plan.close()
