@@ -308,8 +308,9 @@ spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, 
  *   aligned) or in host memory (pinned or pageable); y and u are overwritten
  * With device pointers only, the SpMV then the SpVTM run on `stream`, asynchronously.  Otherwise
  * the library stages the host vectors through its own device buffers on `stream` and on a copy
- * stream of its own: the copy of x to the device overlaps the SpVTM kernels and the copy of u to
- * the host overlaps the SpMV kernels, and the call returns after y and u have landed (work queued
+ * stream of its own: v's copy is queued first, the copy of x to the device overlaps the SpVTM
+ * kernels and the copy of u to the host overlaps the SpMV kernels, and the call returns after y
+ * and u have landed (work queued
  * on `stream` before the call completes first).  Errors as for spmv and spvtm.
  */
 spmv_status spmv_pair(spmv_plan_t plan, const void *x, void *y, const void *v, void *u, void *stream);

@@ -855,10 +855,12 @@ static spmv_status pair_staged(spmv_plan_s *p, const void *x, void *y, const voi
     void *dy = ky == PK_HOST ? p->hout : y, *du = ku == PK_HOST ? p->hu : u;
     // the copy stream starts after the work already queued on s (which may use the buffers)
     step(cudaEventRecord(p->ev_u, s)) && step(cudaStreamWaitEvent(cs, p->ev_u, 0));
+    // v's short copy is queued before x's long one: host-to-device copies share the copy
+    // engines in the order they are issued, and the SpVTM waits for v only
+    if (kv == PK_HOST && step(cudaMemcpyAsync(p->hv, v, yb, cudaMemcpyHostToDevice, s))) dv = p->hv;
     if (kx == PK_HOST && step(cudaMemcpyAsync(p->hin, x, xb, cudaMemcpyHostToDevice, cs)) &&
         step(cudaEventRecord(p->ev_x, cs)))
         dx = p->hin;
-    if (kv == PK_HOST && step(cudaMemcpyAsync(p->hv, v, yb, cudaMemcpyHostToDevice, s))) dv = p->hv;
     if (ce == cudaSuccess) st = run_op(p, SPMV_OP_VTA, 1, &dv, &du, s);
     if (st == SPMV_OK && ku == PK_HOST && step(cudaEventRecord(p->ev_u, s)) && step(cudaStreamWaitEvent(cs, p->ev_u, 0)))
         step(cudaMemcpyAsync(u, p->hu, xb, cudaMemcpyDeviceToHost, cs));
