@@ -798,18 +798,66 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                         chi[b] = s_;
                     }
                 };
-                // the open segment runs through a whole head-free step: add its total
-                auto seg_carry_total = [&](int b, AT t) {
-#pragma unroll
-                    for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
+                // the open segment runs through a whole head-free step: add its total t (the
+                // butterfly over the lanes' sums) to the carry, compensated
+                auto carry_add = [&](int b, AT t) {
                     const AT s_ = chi[b] + t;
                     const AT bp = s_ - chi[b];
                     clo[b] += (chi[b] - (s_ - bp)) + (t - bp);
                     chi[b] = s_;
                 };
+                auto seg_carry_total = [&](int b, AT t) {
+#pragma unroll
+                    for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
+                    carry_add(b, t);
+                };
                 auto run_segdot8 = [&](auto fast_tag, auto full_tag, auto check_tag) {
                     const int nsteps = (rel_hi + 255) >> 8;
-                    for (int stp = 0; stp < nsteps; ++stp) {
+                    int stp = 0;
+                    if constexpr (KB == 1 && sizeof(AT) == 4 && WB <= WARPS_REGS) {
+                        // two steps at a time: their loads, products, lane prefixes and scans do
+                        // not depend on each other and interleave; the carry passes from the
+                        // first step to the second as in the one-step loop (the same operations
+                        // in the same order)
+                        for (; stp + 1 < nsteps; stp += 2) {
+                            int p0a, p0b, basea, baseb;
+                            uint32_t hba, hbb;
+                            AT ra[8][KB], rb[8][KB];
+                            seg_front(full_tag, check_tag, stp, p0a, hba, basea, ra);
+                            seg_front(full_tag, check_tag, stp + 1, p0b, hbb, baseb, rb);
+                            const unsigned bala = __ballot_sync(FULL, hba != 0u);
+                            const unsigned balb = __ballot_sync(FULL, hbb != 0u);
+                            if ((bala | balb) == 0u) {
+                                AT ta = ra[7][0], tb = rb[7][0];
+#pragma unroll
+                                for (int d = 16; d >= 1; d >>= 1) {
+                                    ta += __shfl_xor_sync(FULL, ta, d);
+                                    tb += __shfl_xor_sync(FULL, tb, d);
+                                }
+                                carry_add(0, ta);
+                                carry_add(0, tb);
+                            } else if (bala != 0u && balb != 0u) {
+                                AT Texa, Texb;
+                                const AT Ta = seg_scan(bala, ra[7][0], Texa);
+                                const AT Tb = seg_scan(balb, rb[7][0], Texb);
+                                const AT T31a = __shfl_sync(FULL, Ta, 31);
+                                const AT T31b = __shfl_sync(FULL, Tb, 31);
+                                seg_back(fast_tag, 0, bala, p0a, hba, basea, ra, Texa, T31a);
+                                seg_back(fast_tag, 0, balb, p0b, hbb, baseb, rb, Texb, T31b);
+                            } else if (bala != 0u) {
+                                AT Texa;
+                                const AT Ta = seg_scan(bala, ra[7][0], Texa);
+                                seg_back(fast_tag, 0, bala, p0a, hba, basea, ra, Texa, __shfl_sync(FULL, Ta, 31));
+                                seg_carry_total(0, rb[7][0]);
+                            } else {
+                                seg_carry_total(0, ra[7][0]);
+                                AT Texb;
+                                const AT Tb = seg_scan(balb, rb[7][0], Texb);
+                                seg_back(fast_tag, 0, balb, p0b, hbb, baseb, rb, Texb, __shfl_sync(FULL, Tb, 31));
+                            }
+                        }
+                    }
+                    for (; stp < nsteps; ++stp) {
                         int p0, base;
                         uint32_t hb;
                         AT rr[8][KB];
