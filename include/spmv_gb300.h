@@ -30,6 +30,10 @@
  *    chunk is FP32 for the last three and FP64 for the first; the cross-chunk
  *    combines (the sum of the per-CTA partial vectors of spmv, the overlap-zone
  *    fix-up of spvtm) add in FP64 for every pair, in a fixed order.
+ *  - Infinities and NaNs in the values or vectors give what the plain sum gives
+ *    (an infinity of one sign, or NaN where infinities of both signs or a NaN
+ *    meet), also through the compensated carries of split columns; subnormal
+ *    values and sums are kept (nothing is flushed to zero).
  *  - A plan BORROWS the caller's device arrays ptr/idx/vals: they must stay
  *    allocated and unchanged (values may change between calls) until
  *    spmv_plan_destroy.  The plan owns only its workspace.

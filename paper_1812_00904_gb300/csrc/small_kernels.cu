@@ -19,16 +19,26 @@ struct InPtrs {
     const void *p[VL_MAX];
 };
 
-// An FP32 value widened to FP64 exactly.  Normal numbers by moving the sign, exponent
-// (rebiased from 127 to 1023) and mantissa bits with integer operations, which leaves the
-// FP64 pipe (slow on this part) to the additions; zeros, subnormals, infinities and NaNs by
-// the converting instruction.
+// An FP32 value widened to FP64 exactly, by integer operations on its bits only: the FP64
+// pipe (slow on this part) is left to the additions.  Normal numbers move the sign, the
+// exponent (rebiased from 127 to 1023) and the mantissa; a subnormal m 2^-149 is normalised
+// at its leading one bit h (exponent h - 149); zeros keep their sign; infinities and NaNs
+// take the all-ones exponent with the mantissa bits (a NaN stays a NaN).
 __device__ __forceinline__ double widen(float f) {
     const uint32_t u = __float_as_uint(f);
     const uint32_t e = (u >> 23) & 0xFFu;
-    if (e == 0u || e == 0xFFu) return static_cast<double>(f);
-    const uint64_t d = (static_cast<uint64_t>(u & 0x80000000u) << 32) | (static_cast<uint64_t>(e + 896u) << 52) |
-                       (static_cast<uint64_t>(u & 0x7FFFFFu) << 29);
+    const uint32_t mant = u & 0x7FFFFFu;
+    const uint64_t sign = static_cast<uint64_t>(u & 0x80000000u) << 32;
+    uint64_t d;
+    if (e == 0u) {
+        const int h = 31 - __clz(mant | 1u);
+        d = mant == 0u ? sign
+                       : sign | (static_cast<uint64_t>(h + 874) << 52) |
+                             (static_cast<uint64_t>(mant ^ (1u << h)) << (52 - h));
+    } else {
+        const uint64_t ed = e == 0xFFu ? 0x7FFull : static_cast<uint64_t>(e + 896u);
+        d = sign | (ed << 52) | (static_cast<uint64_t>(mant) << 29);
+    }
     return __longlong_as_double(static_cast<long long>(d));
 }
 __device__ __forceinline__ double widen(double f) { return f; }

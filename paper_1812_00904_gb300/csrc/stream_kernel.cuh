@@ -60,6 +60,17 @@ template <typename XT> __device__ __forceinline__ XT zero_of() { return XT(0); }
 // segmented passes round every product the same way whatever code surrounds it.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+// hi + lo += t, compensated (TwoSum: hi takes the rounded sum, lo gathers its rounding
+// errors).  A sum that is infinite or NaN carries no error term, so that hi + lo stays what the
+// plain sum gives (an infinity would otherwise make the error term NaN).
+template <typename AT>
+__device__ __forceinline__ void carry_in(AT &hi, AT &lo, AT t) {
+    const AT s_ = hi + t;
+    const AT bp = s_ - hi;
+    const AT err = (hi - (s_ - bp)) + (t - bp);
+    lo += isfinite(s_) ? err : AT(0);
+    hi = s_;
+}
 
 // carry records: (hi, lo) of the accumulation type, widened to FP64 by the zone fixup
 template <typename T> struct Pair;
@@ -791,21 +802,13 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                     if (bal) {
                         chi[b] = T31;
                         clo[b] = AT(0);
-                    } else {  // compensated addition (TwoSum) of the step total
-                        const AT s_ = chi[b] + T31;
-                        const AT bp = s_ - chi[b];
-                        clo[b] += (chi[b] - (s_ - bp)) + (T31 - bp);
-                        chi[b] = s_;
+                    } else {  // compensated addition of the step total
+                        carry_in(chi[b], clo[b], T31);
                     }
                 };
                 // the open segment runs through a whole head-free step: add its total t (the
                 // butterfly over the lanes' sums) to the carry, compensated
-                auto carry_add = [&](int b, AT t) {
-                    const AT s_ = chi[b] + t;
-                    const AT bp = s_ - chi[b];
-                    clo[b] += (chi[b] - (s_ - bp)) + (t - bp);
-                    chi[b] = s_;
-                };
+                auto carry_add = [&](int b, AT t) { carry_in(chi[b], clo[b], t); };
                 auto seg_carry_total = [&](int b, AT t) {
 #pragma unroll
                     for (int d = 16; d >= 1; d >>= 1) t += __shfl_xor_sync(FULL, t, d);
@@ -1030,10 +1033,7 @@ __global__ void __launch_bounds__(WB * 32, 1) stream_kernel(const __grid_constan
                             AT tot = t[0];
 #pragma unroll
                             for (int d = NG / 2; d >= 1; d >>= 1) tot = tot + __shfl_xor_sync(FULL, tot, d * VL);
-                            const AT s_ = chi[0] + tot;
-                            const AT bp = s_ - chi[0];
-                            clo[0] += (chi[0] - (s_ - bp)) + (tot - bp);
-                            chi[0] = s_;
+                            carry_in(chi[0], clo[0], tot);
                             continue;
                         }
                         // step with heads: every virtual lane's open sum at its end (T), the open sum
