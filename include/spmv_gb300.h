@@ -310,12 +310,14 @@ spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, 
  * first's result.  No counterpart in the paper beyond the two products.
  *   x (n), y (m), v (m), u (n): vectors of the plan's vector type, each on the device (16-byte
  *   aligned) or in host memory (pinned or pageable); y and u are overwritten
- * With device pointers only, the SpMV then the SpVTM run on `stream`, asynchronously.  Otherwise
- * the library stages the host vectors through its own device buffers on `stream` and on a copy
+ * With device pointers only, the call is asynchronous: the SpMV runs on `stream` and the SpVTM
+ * beside it on a stream of the plan, forked after the work already queued on `stream` and joined
+ * back into it (work queued on `stream` after the call sees both results).  Otherwise the
+ * library stages the host vectors through its own device buffers on `stream` and on a copy
  * stream of its own: v's copy is queued first, the copy of x to the device overlaps the SpVTM
  * kernels and the copy of u to the host overlaps the SpMV kernels, and the call returns after y
- * and u have landed (work queued
- * on `stream` before the call completes first).  Errors as for spmv and spvtm.
+ * and u have landed (work queued on `stream` before the call completes first).  Errors as for
+ * spmv and spvtm.
  */
 spmv_status spmv_pair(spmv_plan_t plan, const void *x, void *y, const void *v, void *u, void *stream);
 

@@ -877,6 +877,33 @@ static spmv_status pair_staged(spmv_plan_s *p, const void *x, void *y, const voi
     return SPMV_OK;
 }
 
+// The two products of a pair with device vectors: the SpMV on `s`, the SpVTM on the plan's
+// second stream, forked after the work queued on `s` and joined back into it.  They use
+// disjoint parts of the workspace (per-CTA partials, carry records), and running side by side
+// lets the short combine and fix-up kernels, and the tail of either pass, overlap the other.
+// Asynchronous; whatever fails, the join is recorded so that `s` never runs ahead of the fork.
+static spmv_status pair_device(spmv_plan_s *p, const void *x, void *y, const void *v, void *u, cudaStream_t s) {
+    if (!p->cstream) CUDA_TRY(cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking));
+    if (!p->ev_x) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_x, cudaEventDisableTiming));
+    if (!p->ev_u) CUDA_TRY(cudaEventCreateWithFlags(&p->ev_u, cudaEventDisableTiming));
+    cudaStream_t cs = p->cstream;
+    CUDA_TRY(cudaEventRecord(p->ev_u, s));
+    CUDA_TRY(cudaStreamWaitEvent(cs, p->ev_u, 0));
+    spmv_status st_u = run_op(p, SPMV_OP_VTA, 1, &v, &u, cs);
+    const std::string msg_u = st_u == SPMV_OK ? std::string() : std::string(spmv_last_error());
+    spmv_status st_y = run_op(p, SPMV_OP_AX, 1, &x, &y, s);
+    const cudaError_t e1 = cudaEventRecord(p->ev_x, cs);
+    const cudaError_t e2 = e1 == cudaSuccess ? cudaStreamWaitEvent(s, p->ev_x, 0) : e1;
+    if (e2 != cudaSuccess) {  // the join could not be queued: wait for the second stream here
+        cudaStreamSynchronize(cs);
+        if (st_y == SPMV_OK && st_u == SPMV_OK)
+            return set_error(SPMV_ERR_CUDA, std::string("spmv_pair: ") + cudaGetErrorString(e2));
+    }
+    if (st_y != SPMV_OK) return st_y;
+    if (st_u != SPMV_OK) return set_error(st_u, msg_u);
+    return SPMV_OK;
+}
+
 spmv_status spmv_pair(spmv_plan_t p, const void *x, void *y, const void *v, void *u, void *stream) {
     if (!p) return set_error(SPMV_ERR_INVALID_ARG, "null plan");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -890,12 +917,8 @@ spmv_status spmv_pair(spmv_plan_t p, const void *x, void *y, const void *v, void
     for (int i = 0; i < 4; ++i)
         if (kinds[i] == PK_DEVICE && ptrs[i] && !aligned16(ptrs[i]))
             return set_error(SPMV_ERR_INVALID_ARG, "device vector pointers must be 16-byte aligned");
-    if (kx == PK_DEVICE && ky == PK_DEVICE && kv == PK_DEVICE && ku == PK_DEVICE) {
-        spmv_status st = run_op(p, SPMV_OP_AX, 1, &x, &y, s);
-        if (st != SPMV_OK) return st;
-        return run_op(p, SPMV_OP_VTA, 1, &v, &u, s);
-    }
     std::lock_guard<std::mutex> lk(p->host_mu);
+    if (kx == PK_DEVICE && ky == PK_DEVICE && kv == PK_DEVICE && ku == PK_DEVICE) return pair_device(p, x, y, v, u, s);
     return pair_staged(p, x, y, v, u, kx, ky, kv, ku, s);
 }
 

@@ -1,5 +1,6 @@
 """spmv_pair: y = A x and u = v^T A for independent x and v in one call, with device vectors
-(two ordered launches) and with host vectors (staged, the transfers of each product overlapping
+(the two products side by side on the caller's stream and a stream of the plan, joined back
+into the caller's) and with host vectors (staged, the transfers of each product overlapping
 the other's kernels).  Results must match the FP64 oracle and the separate calls (bit for bit
 in the segmented direction, whose sums are formed in a fixed order)."""
 import numpy as np
@@ -60,6 +61,33 @@ def test_pair_matches_the_oracle_and_the_separate_calls(layout, where):
     seg = u if layout == "csc" else y
     seg_ref = host_of(ref_u if layout == "csc" else ref_y)
     assert np.array_equal(seg, seg_ref), "segmented direction differs from the separate call"
+    plan.check()
+    plan.close()
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+def test_device_pair_is_ordered_on_the_callers_stream(layout):
+    """Work queued on the caller's stream before the call (here: the inputs' producer) runs
+    before both products, and work queued after it (the results' consumer) sees both results,
+    call after call with no host synchronisation in between."""
+    A, plan, stored, x, v = _case(layout)
+    s = torch.cuda.Stream()
+    x0, v0 = dev_vec(x, torch.float32), dev_vec(v, torch.float32)
+    torch.cuda.synchronize()
+    outs = []
+    with torch.cuda.stream(s):
+        for rep in range(6):
+            xa = x0 * float(rep + 1)
+            va = v0 * float(rep - 2.5)
+            ya, ua = torch.empty(A.m, device=DEV), torch.empty(A.n, device=DEV)
+            pkg.spmv_pair(plan.handle, xa, ya, va, ua, s)
+            outs.append((xa, va, ya.clone(), ua.clone(), ya, ua))
+            ya.fill_(float("nan"))  # overwritten on the stream once the consumer has copied them
+            ua.fill_(float("nan"))
+    s.synchronize()
+    for rep, (xa, va, y, u, _, _) in enumerate(outs):
+        _check(stored, host_of(xa).astype(np.float32), host_of(va).astype(np.float32), host_of(y), host_of(u),
+               f"{layout} call {rep}")
     plan.check()
     plan.close()
 

@@ -127,13 +127,15 @@ def test_subnormal_products_add_exactly_in_the_atomic_pass(layout):
 def test_subnormal_partials_combine_exactly_over_row_blocks():
     """The accumulating direction over the row-sorted copy: segmented block sums of subnormal
     products, then the FP64 combine of the blocks' FP32 partials (widened exactly)."""
-    A = _tiny_matrix("csc", 8)
+    B = _matrix("csc", 400_000, 500, 8, {})  # about 16 nonzeros per (block, row) segment
+    sign = np.where(np.random.default_rng(8).random(B.nnz) < 0.5, -1.0, 1.0)
+    A = synth.SparseMatrix(B.layout, B.m, B.n, B.ptr, B.idx, TINY * sign)
     plan, stored = make_plan(A, torch.float32, flags=pkg.SPMV_PLAN_ROW_BLOCKS)
     assert plan.info()["row_blocks"] > 0
     x = dev_vec(_signs(A.n, 9), torch.float32)
     y = plan.spmv(x)
     plan.check()
     ref = oracle.spmv(stored, host_of(x))
-    assert np.count_nonzero(ref) > 1000
+    assert np.count_nonzero(ref) > 400
     assert torch.equal(y.cpu(), torch.from_numpy(ref).float()), "combined subnormal partials differ from the exact sums"
     plan.close()
