@@ -309,7 +309,8 @@ spmv_status spmv_noalloc(int64_t m, int64_t n, int64_t nnz, const int32_t *ptr, 
  * call: the paper's SpMV-SpVTM pair (Sec. V) where the second product does not consume the
  * first's result.  No counterpart in the paper beyond the two products.
  *   x (n), y (m), v (m), u (n): vectors of the plan's vector type, each on the device (16-byte
- *   aligned) or in host memory (pinned or pageable); y and u are overwritten
+ *   aligned) or in host memory (pinned or pageable); y and u are overwritten.  The four must not
+ *   overlap: the two products may run at the same time.
  * With device pointers only, the call is asynchronous: the SpMV runs on `stream` and the SpVTM
  * beside it on a stream of the plan, forked after the work already queued on `stream` and joined
  * back into it (work queued on `stream` after the call sees both results).  Otherwise the
