@@ -110,12 +110,14 @@ def test_pair_repeated_calls_and_errors():
     plan.close()
 
 
+@pytest.mark.parametrize("where", ["host", "device"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.bfloat16], ids=str)
-@pytest.mark.parametrize("flags", [0, pkg.SPMV_PLAN_ROW_BLOCKS, pkg.SPMV_PLAN_BANK_ORDER],
-                         ids=["stored", "row_blocks", "bank_order"])
-def test_pair_value_types_and_plan_copies(dtype, flags):
-    """Host-staged pairs on FP64 and BF16-value plans, and on plans that multiply their own
-    copies of the nonzeros (row-sorted blocks, bank order), against the FP64 oracle."""
+@pytest.mark.parametrize("flags", [0, pkg.SPMV_PLAN_ROW_BLOCKS, pkg.SPMV_PLAN_BANK_ORDER, pkg.SPMV_PLAN_PROFILE],
+                         ids=["stored", "row_blocks", "bank_order", "profiled"])
+def test_pair_value_types_and_plan_copies(dtype, flags, where):
+    """Pairs (host-staged, and device vectors with the two products side by side) on FP64 and
+    BF16-value plans, on plans that multiply their own copies of the nonzeros (row-sorted
+    blocks, bank order) and with every launch timed, against the FP64 oracle."""
     from gpu_util import TOL, vec_dtype_for
 
     A = synth.random_matrix(1500, 80_000, "csc", density=0.003, seed=81)
@@ -123,13 +125,39 @@ def test_pair_value_types_and_plan_copies(dtype, flags):
     vt = vec_dtype_for(dtype)
     x = synth.uniform_vector(A.n, 82)
     v = synth.uniform_vector(A.m, 83)
-    xh = torch.from_numpy(x).to(vt).pin_memory()
-    vh = torch.from_numpy(v).to(vt).pin_memory()
-    yh = torch.empty(A.m, dtype=vt).pin_memory()
-    uh = torch.empty(A.n, dtype=vt).pin_memory()
-    pkg.spmv_pair(plan.handle, xh, yh, vh, uh)
-    xs, vs = xh.double().numpy(), vh.double().numpy()
-    assert_close(yh.double().numpy(), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), TOL[dtype], "pair y")
-    assert_close(uh.double().numpy(), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), TOL[dtype], "pair u")
+    if where == "host":
+        xa = torch.from_numpy(x).to(vt).pin_memory()
+        va = torch.from_numpy(v).to(vt).pin_memory()
+        ya = torch.empty(A.m, dtype=vt).pin_memory()
+        ua = torch.empty(A.n, dtype=vt).pin_memory()
+    else:
+        xa, va = dev_vec(x, vt), dev_vec(v, vt)
+        ya, ua = torch.empty(A.m, dtype=vt, device=DEV), torch.empty(A.n, dtype=vt, device=DEV)
+    pkg.spmv_pair(plan.handle, xa, ya, va, ua)
+    torch.cuda.synchronize()
+    xs, vs = host_of(xa), host_of(va)
+    assert_close(host_of(ya), oracle.spmv(stored, xs), oracle.abs_spmv(stored, xs), TOL[dtype], "pair y")
+    assert_close(host_of(ua), oracle.spvtm(stored, vs), oracle.abs_spvtm(stored, vs), TOL[dtype], "pair u")
+    if flags == pkg.SPMV_PLAN_PROFILE:  # both products' launches were timed, on either stream
+        assert pkg.spmv_profile_read(plan.handle, 0)[1] == 1 and pkg.spmv_profile_read(plan.handle, 2)[1] == 1
+    plan.check()
+    plan.close()
+
+
+@pytest.mark.parametrize("layout", ["csc", "csr"])
+def test_device_pair_with_the_short_vector_off_chip(layout):
+    """A short dimension too long for shared memory: the accumulating pass adds into a global
+    FP64 accumulator and the segmented pass reads the short vector through L2, side by side."""
+    m, n = (60_000, 40_000) if layout == "csc" else (40_000, 60_000)
+    A = synth.random_matrix(m, n, layout, density=0.0005, seed=91)
+    plan, stored = make_plan(A, torch.float32)
+    assert plan.info()["short_on_chip"] == 0
+    x, v = synth.uniform_vector(n, 92), synth.uniform_vector(m, 93)
+    xd, vd = dev_vec(x, torch.float32), dev_vec(v, torch.float32)
+    y, u = torch.empty(m, device=DEV), torch.empty(n, device=DEV)
+    for _ in range(3):
+        pkg.spmv_pair(plan.handle, xd, y, vd, u)
+    torch.cuda.synchronize()
+    _check(stored, host_of(xd), host_of(vd), host_of(y), host_of(u), f"{layout} off chip")
     plan.check()
     plan.close()
