@@ -37,6 +37,10 @@
  *  - A plan BORROWS the caller's device arrays ptr/idx/vals: they must stay
  *    allocated and unchanged (values may change between calls) until
  *    spmv_plan_destroy.  The plan owns only its workspace.
+ *  - The products of one plan share its workspace (partial vectors, carry records,
+ *    staging buffers): calls on the same plan must not overlap on the device, i.e.
+ *    issue them on one stream or order the streams (spmv_pair runs its two products
+ *    side by side itself).  Different plans are independent.
  *  - Device pointers must be 16-byte aligned (cudaMalloc and torch allocations
  *    are); a misaligned pointer is rejected with SPMV_ERR_INVALID_ARG.
  *  - Vector arguments of spmv, spvtm and spmv_dvalues may be device pointers or
