@@ -196,9 +196,10 @@ spmv_status spmv_plan_ex(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, in
  * With SPMV_PLAN_COO_UNSORTED the triples may come in any order: a stable device
  * radix sort by (major, minor) puts them in storage order in a plan-owned copy, and
  * rows, cols and vals are not read after the call returns.
- * Synchronizes `stream` once.  Errors: SPMV_ERR_BAD_MATRIX when a major index (or,
- * unsorted, either index) is out of range or a sorted stream is not sorted by the
- * major index, SPMV_ERR_OOM, then the errors of spmv_plan_ex.
+ * Synchronizes `stream` once for the triples, then as spmv_plan_ex does.  Errors:
+ * SPMV_ERR_BAD_MATRIX when a major index (or, unsorted, either index) is out of
+ * range or a sorted stream is not sorted by the major index, SPMV_ERR_OOM, then the
+ * errors of spmv_plan_ex.
  */
 spmv_status spmv_plan_coo(spmv_plan_t *out, int64_t m, int64_t n, int64_t nnz, int32_t layout,
                           const int32_t *rows, const int32_t *cols, const void *vals, int32_t val_dtype,
