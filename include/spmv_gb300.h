@@ -100,7 +100,8 @@ typedef struct spmv_plan_s *spmv_plan_t;
 #define SPMV_PLAN_ROW_BLOCKS 0x20u   /* keep a second plan-owned copy of the nonzeros for the product that
                                        accumulates into the short vector (y = A x of a wide CSC matrix,
                                        u^T = v^T A of a tall CSR one): the nonzeros are cut into blocks of
-                                       whole tiles (a multiple of the SM count, one per CTA) and sorted inside
+                                       whole tiles (a multiple of the SM count; a CTA runs one or more in
+                                       turn) and sorted inside
                                        each block by their short-vector index, so that product runs as
                                        segmented dot products over each block's window of the long vector in
                                        shared memory, without atomics and bitwise reproducibly, and the
